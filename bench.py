@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the Hash Chain (HC) searching phase on GB300.
+
+Workload (one "step"): the plain-HC sweep -- four 256 MiB texts drawn i.i.d.
+uniform over sigma in {2, 4, 20, 95} symbols, and for each sigma the pattern
+lengths m in {2, 4, ..., 1024}; P patterns per (sigma, m) cell (default 100),
+each copied from its text at a seeded offset; (q, alpha) as the paper sets
+them for that text type and m.  Every pattern is searched over its whole text
+and all occurrence positions are produced, in text order.
+
+Metric: text GB/s searched (bytes of text / device time, 1e9), device-timed
+with CUDA events on the launching stream, texts resident in HBM; the texts
+(256 MiB) are larger than the 129 MB L2, so no flush is needed.  Also
+reported: GB/s per cell, the roofline fraction of the search kernel against
+the measured HBM bandwidth, an end-to-end figure through the synchronous
+C-ABI call with host buffers (host->device text copies and device->host
+position reads inside the timed region), the CPU oracle's throughput on the
+host cores, and SM clocks sampled during the timed region.
+
+``--impl reference`` times the CPU oracle (the plain C HC of the paper's
+Fig. 4/5) instead, on a bounded sample of the same workload.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torchrun, one process per GPU, each searching the full sweep (weak scaling,
+no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import hc_inputs as hi  # noqa: E402
+
+GB = 1e9
+METRIC = "text GB/s searched (device-timed), plain HC sweep"
+UNIT = "GB/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--patterns", type=int, default=100, help="patterns per (sigma, m) cell")
+    ap.add_argument("--n", type=int, default=1 << 28, help="text length per sigma")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_config(args):
+    return {
+        "workload": "plain HC sweep",
+        "text_bytes_per_sigma": args.n,
+        "sigmas": list(hi.SWEEP_SIGMAS),
+        "ms": list(hi.SWEEP_MS),
+        "patterns_per_cell": args.patterns,
+        "text": "i.i.d. uniform uint8, seeds 100+sigma; patterns copied from the text",
+        "q_alpha": "paper's choice per text type and m (Tables 1-3), q clamped to m",
+        "l2": "inputs larger than L2 (256 MiB texts vs 129 MB L2); no flush",
+    }
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(texts, cells, seconds: float, threads: int):
+    """The oracle's HC (plain C, unmodified) on the host cores: a bounded
+    sample of the sweep -- a prefix of each text, a few patterns per cell --
+    until about `seconds` of wall time; returns text GB/s."""
+    import oracle
+    oracle.build()
+    prefix = 1 << 24
+    total_bytes, total_t, searched = 0, 0.0, 0
+    k = 0
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < seconds:
+        for (sigma, m), pats in cells.items():
+            y = texts[sigma][:prefix]
+            x = pats[k % len(pats)]
+            q, alpha = hi.paper_q_alpha(sigma, m)
+            t0 = time.perf_counter()
+            oracle.hc_search_threaded(x, y, q, alpha, threads)
+            total_t += time.perf_counter() - t0
+            total_bytes += y.size
+            searched += 1
+        k += 1
+    return {"value": total_bytes / total_t / GB, "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": f"{searched} searches: {len(cells)} cells x {k} pattern(s) each, "
+                      f"first {prefix >> 20} MiB of each 256 MiB text, "
+                      f"{threads} threads over pieces overlapping by m-1"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle as the reference arm."""
+    if rank != 0:
+        return
+    texts = {s: hi.sweep_text(s, args.n) for s in hi.SWEEP_SIGMAS}
+    cells = {(s, m): hi.sweep_patterns(texts[s], s, m, max(1, min(args.patterns, 4)))
+             for s in hi.SWEEP_SIGMAS for m in hi.SWEEP_MS}
+    threads = os.cpu_count() or 1
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(texts, cells, 0.5, threads)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(texts, cells, per_step, threads))
+    wall = time.perf_counter() - t0
+    v = float(np.mean([c["value"] for c in vals]))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": workload_config(args),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": vals[-1]["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2310_15711_gb300 as hc
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    hc.build()
+    hc.lib()
+
+    # ---- inputs
+    texts_np = {s: hi.sweep_text(s, args.n) for s in hi.SWEEP_SIGMAS}
+    texts = {s: torch.from_numpy(t).to(dev) for s, t in texts_np.items()}
+    cells = {}
+    for s in hi.SWEEP_SIGMAS:
+        for m in hi.SWEEP_MS:
+            pats = hi.sweep_patterns(texts_np[s], s, m, args.patterns)
+            q, alpha = hi.paper_q_alpha(s, m)
+            filters = []
+            for x in pats:
+                f = hc.hc_preprocess(x, q, alpha)
+                f.to_device()
+                filters.append(f)
+            cells[(s, m)] = (pats, filters, q, alpha)
+    cap = 1 << 27
+    pos = torch.empty(cap, dtype=torch.int64, device=dev)
+    ncell = len(cells)
+    counts = torch.zeros((ncell, args.patterns), dtype=torch.int64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    keys = list(cells.keys())
+
+    def one_step(record_launch_events=None, cell_events=None):
+        for ci, key in enumerate(keys):
+            pats, filters, q, alpha = cells[key]
+            y = texts[key[0]]
+            if cell_events is not None:
+                cell_events[ci][0].record(stream)
+            for pi, f in enumerate(filters):
+                if record_launch_events is not None:
+                    record_launch_events[ci][pi][0].record(stream)
+                hc.hc_search_async(f, y, pos, counts[ci, pi:pi + 1], cap=cap, stream=stream)
+                if record_launch_events is not None:
+                    record_launch_events[ci][pi][1].record(stream)
+            if cell_events is not None:
+                cell_events[ci][1].record(stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+    stream.synchronize()
+    hc.hc_check_status(stream)
+    cnt = counts.cpu().numpy()
+    if cnt.max() > cap:
+        raise RuntimeError("position buffer too small for this workload")
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    launch_ev = [[[ev(), ev()] for _ in range(args.patterns)] for _ in range(ncell)]
+    cell_ev = [[ev(), ev()] for _ in range(ncell)]
+    step_ev = [[ev(), ev()] for _ in range(args.steps)]
+    launch_ms = np.zeros((ncell, args.patterns))
+    cell_ms = np.zeros(ncell)
+
+    sampler = ClockSampler(local_rank)
+    launches0 = hc.hc_kernel_launches()
+    barrier()
+    sampler.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        step_ev[k][0].record(stream)
+        with torch.cuda.stream(stream):
+            one_step(launch_ev, cell_ev)
+        step_ev[k][1].record(stream)
+        # per-launch and per-cell times of this step (read after the sync below)
+        stream.synchronize()
+        for ci in range(ncell):
+            cell_ms[ci] += cell_ev[ci][0].elapsed_time(cell_ev[ci][1])
+            for pi in range(args.patterns):
+                launch_ms[ci, pi] += launch_ev[ci][pi][0].elapsed_time(launch_ev[ci][pi][1])
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    launches = hc.hc_kernel_launches() - launches0
+    hc.hc_check_status(stream)
+    step_ms = float(sum(e[0].elapsed_time(e[1]) for e in step_ev))
+
+    t_local = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    step_ms_max = float(t_local.item())
+
+    text_bytes_step = sum(texts[s].numel() * args.patterns for (s, m) in keys)
+    value = world * text_bytes_step * args.steps / (step_ms_max / 1e3) / GB
+    ms_per_step = step_ms_max / args.steps
+
+    # roofline of the search kernel: algorithmic bytes = text read + 8 bytes
+    # per position written + pattern and filter, per launch
+    cnt = counts.cpu().numpy()
+    algo_bytes = 0.0
+    per_cell = {}
+    for ci, (s, m) in enumerate(keys):
+        pats, filters, q, alpha = cells[(s, m)]
+        n = texts[s].numel()
+        cb = float(n * args.patterns + 8 * cnt[ci].sum() + args.patterns * (m + 4 * (1 << alpha)))
+        algo_bytes += cb
+        per_cell[f"s{s}_m{m}"] = {
+            "GBps": round(n * args.patterns * args.steps / (cell_ms[ci] / 1e3) / GB, 1),
+            "hbm_frac": None,
+            "occ_per_pattern": float(cnt[ci].mean()),
+        }
+        per_cell[f"s{s}_m{m}"]["hbm_frac"] = round(
+            cb * args.steps / (launch_ms[ci].sum() / 1e3) / GB / measured_peaks()[0], 3)
+    kernel_ms_total = float(launch_ms.sum())
+    achieved = algo_bytes * args.steps / (kernel_ms_total / 1e3) / GB
+    peak, peak_kind = measured_peaks()
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": workload_config(args),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "hc_search_kernel (+ its workspace memset, same event pair)",
+                     "launches_per_step": ncell * args.patterns},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "cells": per_cell,
+        "wall_s_timed": round(wall, 3),
+    }
+
+    # ---- end to end through the synchronous C-ABI call, host buffers
+    if not args.no_e2e:
+        line["e2e"] = e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream)
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(texts_np, {k: v[0] for k, v in cells.items()},
+                                            args.cpu_seconds, os.cpu_count() or 1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for key in keys:
+        for f in cells[key][1]:
+            f.free()
+
+
+def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream):
+    """One sweep step through hc_search (the synchronous C-ABI call): per
+    sigma the text is copied from pinned host memory to the device, every
+    pattern of every cell is searched, and each search's positions are read
+    back to pinned host memory.  Everything inside the timed region."""
+    pinned = {s: torch.from_numpy(t).pin_memory() for s, t in texts_np.items()}
+    y_dev = torch.empty(max(t.numel() for t in pinned.values()), dtype=torch.uint8, device=dev)
+    cap = 1 << 27
+    pos = torch.empty(cap, dtype=torch.int64, device=dev)
+    host_pos = torch.empty(cap, dtype=torch.int64).pin_memory()
+    h2d = d2h = 0
+    text_bytes = 0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for s in hi.SWEEP_SIGMAS:
+            n = pinned[s].numel()
+            y_dev[:n].copy_(pinned[s], non_blocking=True)
+            h2d += n
+            for key in keys:
+                if key[0] != s:
+                    continue
+                pats, filters, q, alpha = cells[key]
+                for x, f in zip(pats, filters):
+                    count = hc.hc_search(f, x, y_dev[:n], pos, cap, stream=stream)
+                    host_pos[:count].copy_(pos[:count], non_blocking=True)
+                    d2h += 8 * count + 8
+                    h2d += len(x)
+                    text_bytes += n
+    stream.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(text_bytes / dt / GB, 2), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "api": "hc_search (synchronous C-ABI call per pattern)"}
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

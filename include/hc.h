@@ -1,0 +1,140 @@
+/*
+ * hc.h -- C ABI of the GB300 (sm_103a) Hash Chain (HC) exact string matcher.
+ *
+ * Method: "Efficient Online String Matching through Linked Weak Factors"
+ * (M. N. Palmer, S. Faro, S. Scafiti; arXiv 2310.15711).  The problem (Sec. 1,
+ * Sec. 2): report every occurrence of a pattern x of length m in a text y of
+ * length n, i.e. every window start p in [0, n-m] with y[p..p+m-1] = x.
+ *
+ * Conventions shared by every entry point:
+ *   - Bytes are unsigned (0..255).  A filter word has w = 32 bits.
+ *   - Positions are 0-based window starts, uint64, strictly ascending.
+ *   - Pointers named *_dev are CUDA device pointers (any allocation the
+ *     current device can read/write); all others are host pointers.  The
+ *     caller owns every buffer it passes; the library never frees them and
+ *     never writes to the text.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     work is enqueued on it; entry points without the _async suffix also wait
+ *     for it.
+ *   - Return value: HC_OK (0) or one of the HC_ERR_* codes below;
+ *     hc_last_error() gives a message for the calling thread's last failure.
+ *   - Parameter ranges: m >= 1, 1 <= q <= min(m, 8), 1 <= alpha <= 15.  The
+ *     paper's experiments use 1 <= q <= 8 and 8 <= alpha <= 12 (Sec. 4).
+ */
+#ifndef HC_GB300_H
+#define HC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hc_filter hc_filter;      /* opaque: F, s, F', H_v, q, alpha, x */
+typedef struct CUstream_st *hc_stream_t; /* same type as cudaStream_t */
+
+enum {
+    HC_OK = 0,
+    HC_ERR_ARG = 1,       /* null pointer or parameter out of range */
+    HC_ERR_CAPACITY = 2,  /* more occurrences than the output buffer holds */
+    HC_ERR_CUDA = 3,      /* a CUDA runtime call failed (see hc_last_error) */
+    HC_ERR_NOMEM = 4,     /* host or device allocation failed */
+    HC_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    HC_ERR_ADMISSION = 6, /* server: request refused by the memory budget */
+    HC_ERR_STATE = 7      /* object used in the wrong state */
+};
+
+/* Library version (major*10000 + minor*100 + patch). */
+int hc_version(void);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char *hc_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Preprocessing phase (Sec. 3.1, Eq. 1-5, Fig. 4).
+ *
+ * hc_preprocess builds the filter of pattern x (host memory, m bytes) on the
+ * host: F is a table of 2^alpha 32-bit words; for every pair u1.u2 of
+ * adjacent non-overlapping q-grams of x, F[h(u2)] |= lambda(h(u1)) (Eq. 1);
+ * then every first q-gram u (starting at 0 .. min(q, m-q+1)-1) whose word is
+ * still empty gets F[h(u)] = 1 (Eq. 2 with the first optimisation of
+ * Sec. 3.4).  h is the shift-then-add hash (Eq. 3) with s = floor(alpha/q)
+ * (Eq. 4) taken mod 2^alpha; lambda(v) = 1 << (v mod 32) (Eq. 5).  H_v is
+ * h of the first q-gram of the chain ending at m-1, i.e. of x[m mod q ..]
+ * (Sec. 3.4, second optimisation).
+ * On success *out receives a filter owned by the caller (free it with
+ * hc_filter_free).  Needs no GPU.  Errors: HC_ERR_ARG, HC_ERR_NOMEM.
+ */
+int hc_preprocess(const uint8_t *x, size_t m, int q, int alpha,
+                  hc_filter **out);
+
+/* Frees a filter and its device copy (if one was made).  NULL is a no-op. */
+void hc_filter_free(hc_filter *f);
+
+/* Read-only view of the filter: *F receives a pointer to its 2^alpha words
+ * (valid until hc_filter_free), *nwords = 2^alpha, *hv = H_v.  Any output
+ * pointer may be NULL.  Errors: HC_ERR_ARG. */
+int hc_filter_words(const hc_filter *f, const uint32_t **F, size_t *nwords,
+                    uint32_t *hv);
+
+/* Parameters of a filter: pattern length m, q, alpha and s = floor(alpha/q).
+ * Any output pointer may be NULL.  Errors: HC_ERR_ARG. */
+int hc_filter_params(const hc_filter *f, size_t *m, int *q, int *alpha,
+                     int *s);
+
+/* Copies the filter (F words and pattern bytes) to the current device, once
+ * per filter; later calls are no-ops.  hc_search does this itself on first
+ * use; call it beforehand when the first search must not allocate (e.g.
+ * before capturing a CUDA graph).  Errors: HC_ERR_CUDA, HC_ERR_NOMEM. */
+int hc_filter_to_device(hc_filter *f);
+
+/* ------------------------------------------------------------------------
+ * Searching phase (Sec. 3.3, Fig. 5 left, with the H_v early reject of
+ * Sec. 3.4).  Each length-m window is read backwards q-gram by q-gram: the
+ * q-gram at the window end must hit a non-empty word of F, every q-gram to
+ * its left must be linked to its right neighbour (its lambda bit set in the
+ * neighbour's word); the window shifts on the first miss (by m-q+1 on a
+ * first-test miss, past the unlinked q-gram otherwise), and a window read in
+ * full whose last hash equals H_v is verified byte by byte against x and then
+ * advanced by one.  The result is exactly the set of occurrences.
+ *
+ * hc_search_async: y_dev is the text (n bytes, device memory, any alignment);
+ * pos_dev receives the first min(count, cap) occurrence positions in
+ * ascending order (may be NULL when cap = 0); count_dev (device memory, one
+ * uint64) receives the total count.  Nothing is waited for.  The first call
+ * with a filter copies it to the device (see hc_filter_to_device).  Each call
+ * allocates and releases a small stream-ordered workspace (8 bytes per 16-64
+ * KiB of text) from the device's default memory pool.  n < m is not an error:
+ * the count is 0.  Errors: HC_ERR_ARG, HC_ERR_CUDA, HC_ERR_NOMEM; a device
+ * wait that gave up is reported by the next hc_search/hc_check_status.
+ */
+int hc_search_async(const hc_filter *f, const uint8_t *y_dev, size_t n,
+                    uint64_t *pos_dev, size_t cap, uint64_t *count_dev,
+                    hc_stream_t stream);
+
+/* hc_search: the synchronous form named after the paper's HC(x, m, y, n, q,
+ * alpha).  x (host, the filter's m pattern bytes) must be the pattern the
+ * filter was built from, else HC_ERR_ARG.  Runs hc_search_async, waits for
+ * the stream and stores the total number of occurrences in *count (host).
+ * Returns HC_ERR_CAPACITY (after writing the first cap positions) when the
+ * total exceeds cap; call with cap = 0 to size the buffer.  Errors:
+ * HC_ERR_ARG, HC_ERR_CAPACITY, HC_ERR_CUDA, HC_ERR_NOMEM, HC_ERR_TIMEOUT. */
+int hc_search(const hc_filter *f, const uint8_t *x, const uint8_t *y_dev,
+              size_t n, uint64_t *pos_dev, size_t cap, size_t *count,
+              hc_stream_t stream);
+
+/* Waits for `stream` and reports (and clears) any device-side error flag
+ * raised by the library's kernels on the current device: HC_ERR_TIMEOUT if a
+ * bounded wait gave up, else HC_OK.  Errors: HC_ERR_CUDA. */
+int hc_check_status(hc_stream_t stream);
+
+/* Number of launches of the library's own kernels issued so far by this
+ * process (all devices, all entry points). */
+uint64_t hc_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HC_GB300_H */

@@ -1,0 +1,234 @@
+"""Python binding of libhc, the GB300 (sm_103a) Hash Chain string matcher.
+
+Argument marshalling only: every step of the search runs in the library's
+CUDA kernels (``include/hc.h`` documents the C ABI; the names here are the
+same).  PyTorch supplies device memory and streams.  There is no CPU fallback:
+if ``libhc.so`` has not been built, every call raises.
+
+Method: "Efficient Online String Matching through Linked Weak Factors"
+(Palmer, Faro, Scafiti; arXiv 2310.15711): preprocessing Sec. 3.1 (Eq. 1-5,
+Fig. 4), searching phase Sec. 3.3 (Fig. 5), optimisations Sec. 3.4.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB_PATH
+
+HC_OK = 0
+HC_ERR_ARG = 1
+HC_ERR_CAPACITY = 2
+HC_ERR_CUDA = 3
+HC_ERR_NOMEM = 4
+HC_ERR_TIMEOUT = 5
+HC_ERR_ADMISSION = 6
+HC_ERR_STATE = 7
+
+_ERR_NAMES = {1: "HC_ERR_ARG", 2: "HC_ERR_CAPACITY", 3: "HC_ERR_CUDA", 4: "HC_ERR_NOMEM",
+              5: "HC_ERR_TIMEOUT", 6: "HC_ERR_ADMISSION", 7: "HC_ERR_STATE"}
+
+
+class HCError(RuntimeError):
+    """A libhc call returned an error code."""
+
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+_c_u8p = ctypes.c_void_p
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+
+# name -> (restype, argtypes); the full set of symbols declared in include/hc.h
+SIGNATURES = {
+    "hc_version": (ctypes.c_int, []),
+    "hc_last_error": (ctypes.c_char_p, []),
+    "hc_preprocess": (ctypes.c_int, [_vp, _sz, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "hc_filter_free": (None, [_vp]),
+    "hc_filter_words": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.POINTER(ctypes.c_uint32)),
+                                       ctypes.POINTER(_sz), ctypes.POINTER(ctypes.c_uint32)]),
+    "hc_filter_params": (ctypes.c_int, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "hc_filter_to_device": (ctypes.c_int, [_vp]),
+    "hc_search_async": (ctypes.c_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp]),
+    "hc_search": (ctypes.c_int, [_vp, _vp, _vp, _sz, _vp, _sz, ctypes.POINTER(_sz), _vp]),
+    "hc_check_status": (ctypes.c_int, [_vp]),
+    "hc_kernel_launches": (ctypes.c_uint64, []),
+}
+
+
+def lib():
+    """The loaded libhc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"libhc.so not found at {LIB_PATH}: build it first "
+                    "(python -c 'import __graft_entry__ as g; g.build()'); "
+                    "there is no CPU fallback")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != HC_OK:
+        msg = lib().hc_last_error()
+        raise HCError(rc, where, msg.decode() if msg else "")
+
+
+def _bytes_arg(x):
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x, dtype=np.uint8).tobytes()
+    elif not isinstance(x, (bytes, bytearray)):
+        x = bytes(x)
+    return bytes(x)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype_bytes=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class HCFilter:
+    """An hc_filter: the result of the preprocessing phase (Sec. 3.1)."""
+
+    def __init__(self, handle: ctypes.c_void_p, x: bytes):
+        self._h = handle
+        self.x = x
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("filter has been freed")
+        return self._h
+
+    def params(self):
+        m, q, a, s = _sz(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().hc_filter_params(self.handle, ctypes.byref(m), ctypes.byref(q),
+                                      ctypes.byref(a), ctypes.byref(s)), "hc_filter_params")
+        return {"m": m.value, "q": q.value, "alpha": a.value, "s": s.value}
+
+    def words(self):
+        """(F as a uint32 numpy copy, H_v)."""
+        p = ctypes.POINTER(ctypes.c_uint32)()
+        nw, hv = _sz(), ctypes.c_uint32()
+        _check(lib().hc_filter_words(self.handle, ctypes.byref(p), ctypes.byref(nw),
+                                     ctypes.byref(hv)), "hc_filter_words")
+        return np.ctypeslib.as_array(p, shape=(nw.value,)).copy(), hv.value
+
+    def to_device(self):
+        _check(lib().hc_filter_to_device(self.handle), "hc_filter_to_device")
+
+    def free(self):
+        if self._h is not None and _lib is not None:
+            _lib.hc_filter_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hc_preprocess(x, q: int, alpha: int) -> HCFilter:
+    """hc_preprocess(x, m, q, alpha): the filter of pattern x (host bytes)."""
+    xb = _bytes_arg(x)
+    out = _vp()
+    buf = ctypes.create_string_buffer(xb, len(xb)) if xb else None
+    _check(lib().hc_preprocess(ctypes.cast(buf, _vp) if buf is not None else None, len(xb),
+                               int(q), int(alpha), ctypes.byref(out)), "hc_preprocess")
+    return HCFilter(out, xb)
+
+
+def hc_search_async(f: HCFilter, y_dev, pos_dev, count_dev, n: int | None = None,
+                    cap: int | None = None, stream=None) -> None:
+    """hc_search_async: enqueue the search of y_dev (uint8 CUDA tensor) on
+    ``stream``; positions go to pos_dev (int64 CUDA tensor holding uint64
+    values, or None), the total to count_dev (int64 CUDA tensor, 1 element)."""
+    n = y_dev.numel() if n is None else int(n)
+    if pos_dev is None:
+        cap = 0
+    elif cap is None:
+        cap = pos_dev.numel()
+    _check(lib().hc_search_async(f.handle, _dev_ptr(y_dev), n, _dev_ptr(pos_dev), int(cap),
+                                 _dev_ptr(count_dev), _stream_handle(stream)),
+           "hc_search_async")
+
+
+def hc_search(f: HCFilter, x, y_dev, pos_dev=None, cap: int | None = None, stream=None,
+              n: int | None = None):
+    """hc_search(filter, x, y, n): synchronous search; returns the total count.
+
+    Writes the first min(count, cap) positions into pos_dev.  Raises HCError
+    with code HC_ERR_CAPACITY if the count exceeds cap (after writing them)."""
+    n = y_dev.numel() if n is None else int(n)
+    if pos_dev is None:
+        cap = 0
+    elif cap is None:
+        cap = pos_dev.numel()
+    xb = _bytes_arg(x)
+    cnt = _sz()
+    xbuf = ctypes.create_string_buffer(xb, len(xb))
+    _check(lib().hc_search(f.handle, ctypes.cast(xbuf, _vp), _dev_ptr(y_dev), n,
+                           _dev_ptr(pos_dev), int(cap), ctypes.byref(cnt), _stream_handle(stream)),
+           "hc_search")
+    return cnt.value
+
+
+def search_positions(f: HCFilter, x, y_dev, stream=None):
+    """All occurrence positions of x in y_dev as an int64 CUDA tensor: one
+    counting call (cap = 0), then one call into a buffer of that size."""
+    import torch
+    count = hc_search(f, x, y_dev, None, 0, stream)
+    pos = torch.empty(max(count, 1), dtype=torch.int64, device=y_dev.device)
+    count2 = hc_search(f, x, y_dev, pos, count, stream)
+    assert count2 == count
+    return pos[:count]
+
+
+def hc_check_status(stream=None) -> None:
+    _check(lib().hc_check_status(_stream_handle(stream)), "hc_check_status")
+
+
+def hc_kernel_launches() -> int:
+    return int(lib().hc_kernel_launches())
+
+
+def hc_version() -> int:
+    return int(lib().hc_version())
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libhc.so for sm_103a (see _build.py)."""
+    return _build.build(force=force, verbose=verbose)

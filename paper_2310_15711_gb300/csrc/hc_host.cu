@@ -1,0 +1,185 @@
+// hc_host.cu -- host side of the library: the preprocessing phase (Sec. 3.1,
+// Eq. 1-5), the filter object, its device copy, error reporting.
+//
+// The filter is built pair by pair rather than chain by chain: every q-gram
+// hash is computed once (Eq. 3, Eq. 4), then every adjacent non-overlapping
+// pair (x[i..i+q-1], x[i+q..i+2q-1]), 0 <= i <= m-2q, ORs lambda(h(left))
+// into F[h(right)] (Eq. 1), then every first q-gram (start < min(q, m-q+1))
+// whose word is still empty gets 1 (Eq. 2, first optimisation of Sec. 3.4).
+// Both steps are order-independent (OR is commutative; the marking step only
+// writes into words that the linking step left empty), so F equals the
+// chain-ordered construction of the paper's Fig. 4 word for word.  H_v is the
+// hash of the first q-gram of the chain ending at m-1, which starts at
+// m mod q (Sec. 3.4).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <unordered_map>
+
+#include "hc_internal.h"
+
+namespace hc {
+
+namespace {
+thread_local std::string t_last_error;
+std::mutex g_dev_mu;
+std::unordered_map<int, DeviceInfo> g_dev_info;
+}  // namespace
+
+std::atomic<uint64_t> g_launches{0};
+
+int set_error(int code, const std::string& msg) {
+  t_last_error = msg;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "%s: %s (%s)", where, cudaGetErrorString(e),
+                cudaGetErrorName(e));
+  t_last_error = buf;
+  return e == cudaErrorMemoryAllocation ? HC_ERR_NOMEM : HC_ERR_CUDA;
+}
+
+void clear_error() { t_last_error.clear(); }
+
+const DeviceInfo& device_info(int dev) {
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  auto it = g_dev_info.find(dev);
+  if (it != g_dev_info.end()) return it->second;
+  DeviceInfo di;
+  cudaDeviceGetAttribute(&di.sm_count, cudaDevAttrMultiProcessorCount, dev);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  di.smem_optin = static_cast<size_t>(optin);
+  return g_dev_info.emplace(dev, di).first->second;
+}
+
+int filter_to_device(Filter* f) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(f->mu);
+  if (f->dev_image != nullptr) {
+    if (f->dev == dev) return HC_OK;
+    return set_error(HC_ERR_STATE,
+                     "filter already resides on another device; build one filter per device");
+  }
+  std::vector<uint8_t> img(f->image_bytes(), 0);
+  std::memcpy(img.data(), f->F.data(), f->F.size() * 4);
+  std::memcpy(img.data() + f->F.size() * 4, f->x.data(), f->m);
+  void* p = nullptr;
+  e = cudaMalloc(&p, img.size());
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(filter image)");
+  e = cudaMemcpy(p, img.data(), img.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    return cuda_error(e, "cudaMemcpy(filter image)");
+  }
+  f->dev_image = static_cast<uint8_t*>(p);
+  f->dev = dev;
+  return HC_OK;
+}
+
+}  // namespace hc
+
+using namespace hc;
+
+extern "C" {
+
+int hc_version(void) { return 100; }
+
+const char* hc_last_error(void) { return t_last_error.c_str(); }
+
+uint64_t hc_kernel_launches(void) { return g_launches.load(); }
+
+int hc_preprocess(const uint8_t* x, size_t m, int q, int alpha, hc_filter** out) {
+  clear_error();
+  if (out == nullptr) return set_error(HC_ERR_ARG, "hc_preprocess: out is NULL");
+  *out = nullptr;
+  if (x == nullptr) return set_error(HC_ERR_ARG, "hc_preprocess: x is NULL");
+  if (m == 0) return set_error(HC_ERR_ARG, "hc_preprocess: m must be >= 1");
+  if (q < 1 || q > kMaxQ || static_cast<size_t>(q) > m)
+    return set_error(HC_ERR_ARG, "hc_preprocess: need 1 <= q <= min(m, 8)");
+  if (alpha < 1 || alpha > kMaxAlpha)
+    return set_error(HC_ERR_ARG, "hc_preprocess: need 1 <= alpha <= 15");
+  if (m > (size_t(1) << 30)) return set_error(HC_ERR_ARG, "hc_preprocess: m above 2^30");
+
+  Filter* f = new (std::nothrow) Filter();
+  if (f == nullptr) return set_error(HC_ERR_NOMEM, "hc_preprocess: out of host memory");
+  try {
+    f->m = m;
+    f->q = q;
+    f->alpha = alpha;
+    f->s = alpha / q;                              // Eq. 4
+    f->mask = (uint32_t(1) << alpha) - 1u;         // mod 2^alpha as an AND
+    f->F.assign(size_t(1) << alpha, 0u);
+    f->x.assign(x, x + m);
+
+    // h of every q-gram, indexed by its start: h(u) = sum_k u[k] * 2^(s*k)
+    // mod 2^alpha (Eq. 3), evaluated from the last character down.
+    const size_t nq = m - static_cast<size_t>(q) + 1;
+    std::vector<uint32_t> h(nq);
+    for (size_t i = 0; i < nq; ++i) {
+      uint32_t v = 0;
+      for (int k = q - 1; k >= 0; --k) v = (v << f->s) + x[i + static_cast<size_t>(k)];
+      h[i] = v & f->mask;
+    }
+    // Eq. 1 for every adjacent non-overlapping pair.
+    for (size_t i = 0; i + 2 * static_cast<size_t>(q) <= m; ++i)
+      f->F[h[i + q]] |= 1u << (h[i] & 31u);
+    // Eq. 2, only into words still empty.
+    const size_t nfirst = std::min(static_cast<size_t>(q), nq);
+    for (size_t i = 0; i < nfirst; ++i)
+      if (f->F[h[i]] == 0) f->F[h[i]] = 1u;
+    f->hv = h[m % static_cast<size_t>(q)];
+  } catch (const std::bad_alloc&) {
+    delete f;
+    return set_error(HC_ERR_NOMEM, "hc_preprocess: out of host memory");
+  }
+  *out = reinterpret_cast<hc_filter*>(f);
+  return HC_OK;
+}
+
+void hc_filter_free(hc_filter* fp) {
+  Filter* f = as_filter(fp);
+  if (f == nullptr) return;
+  if (f->dev_image != nullptr) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != f->dev) cudaSetDevice(f->dev);
+    cudaFree(f->dev_image);
+    if (cur != f->dev) cudaSetDevice(cur);
+  }
+  f->magic = 0;
+  delete f;
+}
+
+int hc_filter_words(const hc_filter* fp, const uint32_t** F, size_t* nwords, uint32_t* hv) {
+  Filter* f = as_filter(fp);
+  if (f == nullptr) return set_error(HC_ERR_ARG, "hc_filter_words: invalid filter");
+  if (F) *F = f->F.data();
+  if (nwords) *nwords = f->F.size();
+  if (hv) *hv = f->hv;
+  return HC_OK;
+}
+
+int hc_filter_params(const hc_filter* fp, size_t* m, int* q, int* alpha, int* s) {
+  Filter* f = as_filter(fp);
+  if (f == nullptr) return set_error(HC_ERR_ARG, "hc_filter_params: invalid filter");
+  if (m) *m = f->m;
+  if (q) *q = f->q;
+  if (alpha) *alpha = f->alpha;
+  if (s) *s = f->s;
+  return HC_OK;
+}
+
+int hc_filter_to_device(hc_filter* fp) {
+  clear_error();
+  Filter* f = as_filter(fp);
+  if (f == nullptr) return set_error(HC_ERR_ARG, "hc_filter_to_device: invalid filter");
+  return filter_to_device(f);
+}
+
+}  // extern "C"

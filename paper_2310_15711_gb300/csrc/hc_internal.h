@@ -1,0 +1,62 @@
+// hc_internal.h -- private declarations shared by the library's translation
+// units (host filter object, error reporting, launch bookkeeping).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hc.h"
+
+namespace hc {
+
+constexpr uint32_t kFilterMagic = 0x48433331u;  // "HC31"
+constexpr int kMaxQ = 8;
+constexpr int kMaxAlpha = 15;
+
+// Host-side filter (Sec. 3.1): F, s, F' (mask), H_v and a copy of x, plus a
+// lazily made device image laid out as [F: 2^alpha uint32][x: m bytes],
+// 16-byte aligned.
+struct Filter {
+  uint32_t magic = kFilterMagic;
+  size_t m = 0;
+  int q = 0, alpha = 0, s = 0;
+  uint32_t mask = 0, hv = 0;
+  std::vector<uint32_t> F;
+  std::vector<uint8_t> x;
+  std::mutex mu;
+  int dev = -1;
+  uint8_t* dev_image = nullptr;  // owned, cudaMalloc'd
+  size_t image_bytes() const { return (F.size() * 4 + m + 15) & ~size_t(15); }
+  const uint32_t* dev_F() const { return reinterpret_cast<const uint32_t*>(dev_image); }
+  const uint8_t* dev_x() const { return dev_image + F.size() * 4; }
+};
+
+inline Filter* as_filter(const hc_filter* f) {
+  auto* p = reinterpret_cast<Filter*>(const_cast<hc_filter*>(f));
+  return (p != nullptr && p->magic == kFilterMagic) ? p : nullptr;
+}
+
+// Error reporting: per-thread last message.
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* where);
+void clear_error();
+
+// Counts launches of this library's kernels.
+extern std::atomic<uint64_t> g_launches;
+
+// Copies the filter to the current device (once).  Returns an HC_* code.
+int filter_to_device(Filter* f);
+
+// Device properties cached per device.
+struct DeviceInfo {
+  int sm_count = 0;
+  size_t smem_optin = 0;
+};
+const DeviceInfo& device_info(int dev);
+
+}  // namespace hc

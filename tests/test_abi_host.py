@@ -1,0 +1,84 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+* libhc.so loads and exports every function that include/hc.h declares, and
+  the binding registers exactly those names.
+* hc_preprocess (host code of the library) builds the same F and H_v as the
+  oracle's Fig. 4 preprocessing, word for word.
+* Invalid arguments are rejected with HC_ERR_ARG.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2310_15711_gb300 as hc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    hc.build()
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for mt in re.finditer(r"^[A-Za-z_][\w \*]*?\b(hc_\w+)\s*\(", src, flags=re.M):
+            names.add(mt.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    declared = _declared_functions()
+    assert {"hc_preprocess", "hc_search", "hc_search_async", "hc_filter_free"} <= declared
+    L = ctypes.CDLL(hc.LIB_PATH)
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(hc.SIGNATURES) == declared
+
+
+def test_version_and_launch_counter():
+    assert hc.hc_version() >= 100
+    assert hc.hc_kernel_launches() >= 0
+
+
+@pytest.mark.parametrize("sigma", [2, 4, 20, 95, 256])
+def test_host_filter_equals_oracle_filter(sigma):
+    rng = np.random.default_rng(sigma)
+    for _ in range(150):
+        m = int(rng.choice([1, 2, 3, 5, 8, 13, 16, 31, 64, 200, 1024]))
+        q = int(rng.integers(1, min(m, 8) + 1))
+        alpha = int(rng.integers(1, 16))
+        x = rng.integers(0, sigma, m, dtype=np.uint16).astype(np.uint8) + (0 if sigma == 256 else 40)
+        f = hc.hc_preprocess(x, q, alpha)
+        F, hv = f.words()
+        ref = oracle.preprocess(x, q, alpha)
+        assert np.array_equal(F, ref["F"]), (m, q, alpha)
+        assert hv == ref["hv"]
+        p = f.params()
+        assert p == {"m": m, "q": q, "alpha": alpha, "s": alpha // q}
+        f.free()
+
+
+def test_preprocess_rejects_invalid_arguments():
+    for x, q, alpha in [(b"abc", 4, 10), (b"abc", 0, 10), (b"abcdefghij", 9, 10),
+                        (b"abc", 2, 0), (b"abc", 2, 16), (b"", 1, 10)]:
+        with pytest.raises(hc.HCError) as ei:
+            hc.hc_preprocess(x, q, alpha)
+        assert ei.value.code == hc.HC_ERR_ARG
+
+
+def test_null_filter_is_rejected():
+    L = hc.lib()
+    assert L.hc_filter_words(None, None, None, None) == hc.HC_ERR_ARG
+    assert L.hc_filter_params(None, None, None, None, None) == hc.HC_ERR_ARG
+    assert L.hc_search_async(None, None, 0, None, 0, None, None) == hc.HC_ERR_ARG
+    L.hc_filter_free(None)  # no-op

@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA search (through the C ABI) against the oracle.
+
+Positions must agree bit for bit (sorted occurrence lists, uint64).  Cases
+span several chunks with ragged tails, every q, alpha from 1 to 15, unaligned
+text pointers, degenerate inputs (n < m, n == m, sigma = 1, m = q, m = 1,
+alpha < q), more occurrences than the per-thread slots hold, the unstaged
+kernel for very long patterns, the capacity error, and the full-size
+workloads (256 MiB sweep texts, the 1 GiB order-2 Markov text) compared in
+full against the oracle's HC.
+"""
+import numpy as np
+import pytest
+
+import hc_inputs as hi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_15711_gb300 as hc
+    hc.build()
+    hc.lib()
+    return hc
+
+
+def _hc():
+    import paper_2310_15711_gb300 as hc
+    return hc
+
+
+def _upload(y: np.ndarray, offset: int = 0):
+    n = y.size
+    buf = torch.empty(n + offset + 32, dtype=torch.uint8, device="cuda")
+    if n:
+        buf[offset:offset + n].copy_(torch.from_numpy(np.ascontiguousarray(y)))
+    return buf[offset:offset + n], buf
+
+
+def gpu_positions(x, y, q, alpha, offset=0):
+    hc = _hc()
+    y_dev, keep = _upload(np.asarray(y, dtype=np.uint8), offset)
+    f = hc.hc_preprocess(x, q, alpha)
+    pos = hc.search_positions(f, x, y_dev)
+    out = pos.cpu().numpy().view(np.uint64).copy()
+    f.free()
+    del keep
+    return out
+
+
+def _case(rng, sigma, n, m, plant):
+    y = (rng.integers(0, sigma, n, dtype=np.uint16) + 65).astype(np.uint8)
+    x = (rng.integers(0, sigma, m, dtype=np.uint16) + 65).astype(np.uint8)
+    if n >= m:
+        for _ in range(plant):
+            off = int(rng.integers(0, n - m + 1))
+            y[off:off + m] = x
+    return x, y
+
+
+def test_config_one_exact():
+    c = hi.config_one()
+    got = gpu_positions(c["x"], c["y"], c["q"], c["alpha"])
+    want = oracle.hc_search(c["x"], c["y"], c["q"], c["alpha"])
+    assert np.array_equal(got, want)
+    assert np.array_equal(want, oracle.naive_search(c["x"], c["y"]))
+    assert c["offset"] in set(got.tolist())
+
+
+@pytest.mark.parametrize("sigma", [1, 2, 4, 20, 95])
+def test_random_cases_all_q(sigma):
+    rng = np.random.default_rng(1000 + sigma)
+    ms = [1, 2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 32, 33, 64, 100, 255, 256, 1000, 1024, 2047]
+    for trial in range(70):
+        m = int(rng.choice(ms))
+        q = int(rng.integers(1, min(m, 8) + 1))
+        alpha = int(rng.choice([1, 3, 4, 8, 11, 12, 13, 15]))
+        n = int(rng.integers(0, 200_000)) if trial % 3 else int(rng.integers(0, 3000))
+        x, y = _case(rng, sigma, n, m, plant=int(rng.integers(0, 40)))
+        offset = int(rng.integers(0, 16))
+        got = gpu_positions(x, y, q, alpha, offset)
+        want = oracle.hc_search(x, y, q, alpha)
+        assert np.array_equal(got, want), (sigma, m, q, alpha, n, offset)
+
+
+def test_degenerate_inputs():
+    cases = [
+        (b"A", b""), (b"ABC", b"AB"), (b"ABC", b"ABC"), (b"ABC", b"ABD"),
+        (b"A", b"A" * 100_000),                  # m = 1, every position
+        (b"AAAA", b"A" * 300_001),               # overlapping, slot overflow
+        (b"AB" * 8, b"AB" * 100_000),            # periodic
+        (b"GATTACA", b"GATTACA" + b"C" * 70_000 + b"GATTACA"),
+    ]
+    for x, y in cases:
+        x = np.frombuffer(x, np.uint8)
+        y = np.frombuffer(y, np.uint8)
+        want = oracle.naive_search(x, y)
+        for q in sorted({1, min(2, x.size), min(4, x.size), min(8, x.size)}):
+            for alpha in (2, 8, 12):
+                for off in (0, 5):
+                    got = gpu_positions(x, y, q, alpha, off)
+                    assert np.array_equal(got, want), (bytes(x[:8]), y.size, q, alpha, off)
+
+
+def test_alpha_below_q_and_large_alpha():
+    rng = np.random.default_rng(77)
+    x, y = _case(rng, 4, 500_000, 24, plant=30)
+    for q, alpha in [(8, 3), (7, 1), (6, 15), (1, 15), (3, 14)]:
+        assert np.array_equal(gpu_positions(x, y, q, alpha), oracle.hc_search(x, y, q, alpha))
+
+
+def test_very_long_pattern_unstaged_kernel():
+    rng = np.random.default_rng(5)
+    x, y = _case(rng, 4, 2_000_000, 20_000, plant=7)
+    for q in (4, 8):
+        got = gpu_positions(x, y, q, 12, offset=3)
+        assert np.array_equal(got, oracle.naive_search(x, y))
+        assert got.size >= 1
+
+
+def test_capacity_error_writes_prefix():
+    hc = _hc()
+    x = np.frombuffer(b"AA", np.uint8)
+    y = np.frombuffer(b"A" * 10_000, np.uint8)
+    y_dev, keep = _upload(y)
+    f = hc.hc_preprocess(x, 2, 10)
+    pos = torch.zeros(100, dtype=torch.int64, device="cuda")
+    with pytest.raises(hc.HCError) as ei:
+        hc.hc_search(f, x, y_dev, pos, 100)
+    assert ei.value.code == hc.HC_ERR_CAPACITY
+    assert pos.cpu().numpy().tolist() == list(range(100))
+    assert hc.hc_search(f, x, y_dev, None, 0) == 9_999
+    with pytest.raises(hc.HCError) as ei:
+        hc.hc_search(f, b"AB", y_dev, None, 0)     # not the filter's pattern
+    assert ei.value.code == hc.HC_ERR_ARG
+
+
+def test_async_entry_point_and_count():
+    hc = _hc()
+    rng = np.random.default_rng(9)
+    x, y = _case(rng, 20, 3_000_000, 12, plant=100)
+    y_dev, keep = _upload(y)
+    f = hc.hc_preprocess(x, 3, 11)
+    want = oracle.hc_search(x, y, 3, 11)
+    pos = torch.full((want.size + 10,), -1, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        hc.hc_search_async(f, y_dev, pos, cnt, stream=s)
+    s.synchronize()
+    hc.hc_check_status(s)
+    assert int(cnt.item()) == want.size
+    assert np.array_equal(pos[:want.size].cpu().numpy().view(np.uint64), want)
+    assert int(pos[want.size].item()) == -1     # nothing written past the count
+
+
+def test_full_size_sweep_texts():
+    """256 MiB sweep texts (i.i.d. uniform), patterns copied from the text,
+    full comparison with the oracle's HC for a cell of each alphabet."""
+    for sigma, m in [(2, 2), (4, 16), (20, 32), (95, 1024)]:
+        y = hi.sweep_text(sigma)
+        x = hi.sweep_patterns(y, sigma, m, count=1)[0]
+        q, alpha = hi.paper_q_alpha(sigma, m)
+        got = gpu_positions(x, y, q, alpha)
+        want = oracle.hc_search(x, y, q, alpha)
+        assert np.array_equal(got, want), (sigma, m)
+        assert got.size >= 1
+        del y
+
+
+def test_full_size_skewed_markov_text():
+    y = hi.skew_text()
+    rng = np.random.default_rng(123)
+    for m in (4, 16, 128):
+        x, _ = hi.extract_pattern(y, m, rng)
+        q, alpha = hi.paper_q_alpha(60, m)
+        got = gpu_positions(x, y, q, alpha)
+        want = oracle.hc_search(x, y, q, alpha)
+        assert np.array_equal(got, want), m
