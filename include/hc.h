@@ -104,14 +104,52 @@ int hc_filter_to_device(hc_filter *f);
  * ascending order (may be NULL when cap = 0); count_dev (device memory, one
  * uint64) receives the total count.  Nothing is waited for.  The first call
  * with a filter copies it to the device (see hc_filter_to_device).  Each call
- * allocates and releases a small stream-ordered workspace (8 bytes per 16-64
- * KiB of text) from the device's default memory pool.  n < m is not an error:
- * the count is 0.  Errors: HC_ERR_ARG, HC_ERR_CUDA, HC_ERR_NOMEM; a device
- * wait that gave up is reported by the next hc_search/hc_check_status.
+ * takes a stream-ordered workspace from the library's memory pool and gives
+ * it back after its kernels: 16 bytes per CTA plus 4 bytes per spilled
+ * position (by default min(n-m+1, max(cap, 2^20)) of them); the pool keeps
+ * freed memory for reuse.  n < m is not an error: the count is 0.  Errors:
+ * HC_ERR_ARG, HC_ERR_CUDA, HC_ERR_NOMEM; a device wait that gave up is
+ * reported by the next hc_search/hc_check_status.
  */
 int hc_search_async(const hc_filter *f, const uint8_t *y_dev, size_t n,
                     uint64_t *pos_dev, size_t cap, uint64_t *count_dev,
                     hc_stream_t stream);
+
+/* Launch options of hc_search_ex (zero = automatic).
+ *   mode: HC_MODE_STAGED -- each thread runs HC over its own run of window
+ *         starts, the text staged in shared memory by bulk copies;
+ *         HC_MODE_DIRECT -- the same, reading the text from global memory
+ *         (long patterns: their shifts skip most of the text);
+ *         HC_MODE_DENSE -- for m = q only, where HC tests every window in
+ *         turn: the lanes of a warp test consecutive windows together.
+ *         HC_MODE_AUTO picks DENSE when m = q, DIRECT when m - q + 1 >= 200,
+ *         else STAGED.  Every mode returns the same positions.
+ *   lane_bytes: window starts per thread and chunk (1..4096, a chunk holds
+ *         256 of them; at most 256 in the dense mode);
+ *   stages: text staging buffers per CTA (2..4);
+ *   ctas_per_sm: upper bound on resident CTAs per SM;
+ *   spill_entries: capacity, in positions, of the per-launch spill regions
+ *         that hold occurrences until their output offsets are known
+ *         (positions that do not fit are found again by a second scan of
+ *         the affected chunks).
+ * struct_size must be sizeof(hc_search_opts). */
+enum { HC_MODE_AUTO = 0, HC_MODE_STAGED = 1, HC_MODE_DIRECT = 2, HC_MODE_DENSE = 3 };
+
+typedef struct hc_search_opts {
+    size_t struct_size;
+    int lane_bytes;
+    int stages;
+    int ctas_per_sm;
+    int mode;
+    uint64_t spill_entries;
+} hc_search_opts;
+
+/* hc_search_ex: hc_search_async with explicit launch options (opts may be
+ * NULL).  Same arguments, results and errors as hc_search_async, plus
+ * HC_ERR_ARG for options out of range.  Used by the autotuner and tests. */
+int hc_search_ex(const hc_filter *f, const uint8_t *y_dev, size_t n,
+                 uint64_t *pos_dev, size_t cap, uint64_t *count_dev,
+                 const hc_search_opts *opts, hc_stream_t stream);
 
 /* hc_search: the synchronous form named after the paper's HC(x, m, y, n, q,
  * alpha).  x (host, the filter's m pattern bytes) must be the pattern the

@@ -62,6 +62,7 @@ SIGNATURES = {
     "hc_filter_to_device": (ctypes.c_int, [_vp]),
     "hc_search_async": (ctypes.c_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp]),
     "hc_search": (ctypes.c_int, [_vp, _vp, _vp, _sz, _vp, _sz, ctypes.POINTER(_sz), _vp]),
+    "hc_search_ex": (ctypes.c_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _vp]),
     "hc_check_status": (ctypes.c_int, [_vp]),
     "hc_kernel_launches": (ctypes.c_uint64, []),
 }
@@ -117,6 +118,23 @@ def _dev_ptr(t, dtype_bytes=None):
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+HC_MODE_AUTO = 0
+HC_MODE_STAGED = 1
+HC_MODE_DIRECT = 2
+HC_MODE_DENSE = 3
+
+
+class SearchOpts(ctypes.Structure):
+    """hc_search_opts (zero = automatic)."""
+    _fields_ = [("struct_size", ctypes.c_size_t), ("lane_bytes", ctypes.c_int),
+                ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("mode", ctypes.c_int), ("spill_entries", ctypes.c_uint64)]
+
+    def __init__(self, lane_bytes=0, stages=0, ctas_per_sm=0, spill_entries=0, mode=0):
+        super().__init__(ctypes.sizeof(SearchOpts), int(lane_bytes), int(stages),
+                         int(ctas_per_sm), int(mode), int(spill_entries))
 
 
 class HCFilter:
@@ -186,12 +204,27 @@ def hc_search_async(f: HCFilter, y_dev, pos_dev, count_dev, n: int | None = None
            "hc_search_async")
 
 
+def hc_search_ex(f: HCFilter, y_dev, pos_dev, count_dev, opts: SearchOpts | None = None,
+                 n: int | None = None, cap: int | None = None, stream=None) -> None:
+    """hc_search_ex: hc_search_async with explicit launch options."""
+    n = y_dev.numel() if n is None else int(n)
+    if pos_dev is None:
+        cap = 0
+    elif cap is None:
+        cap = pos_dev.numel()
+    _check(lib().hc_search_ex(f.handle, _dev_ptr(y_dev), n, _dev_ptr(pos_dev), int(cap),
+                              _dev_ptr(count_dev),
+                              ctypes.byref(opts) if opts is not None else None,
+                              _stream_handle(stream)), "hc_search_ex")
+
+
 def hc_search(f: HCFilter, x, y_dev, pos_dev=None, cap: int | None = None, stream=None,
-              n: int | None = None):
+              n: int | None = None, allow_truncated: bool = False):
     """hc_search(filter, x, y, n): synchronous search; returns the total count.
 
     Writes the first min(count, cap) positions into pos_dev.  Raises HCError
-    with code HC_ERR_CAPACITY if the count exceeds cap (after writing them)."""
+    with code HC_ERR_CAPACITY if the count exceeds cap (after writing them),
+    unless ``allow_truncated`` is set (e.g. cap = 0 to size a buffer)."""
     n = y_dev.numel() if n is None else int(n)
     if pos_dev is None:
         cap = 0
@@ -200,9 +233,10 @@ def hc_search(f: HCFilter, x, y_dev, pos_dev=None, cap: int | None = None, strea
     xb = _bytes_arg(x)
     cnt = _sz()
     xbuf = ctypes.create_string_buffer(xb, len(xb))
-    _check(lib().hc_search(f.handle, ctypes.cast(xbuf, _vp), _dev_ptr(y_dev), n,
-                           _dev_ptr(pos_dev), int(cap), ctypes.byref(cnt), _stream_handle(stream)),
-           "hc_search")
+    rc = lib().hc_search(f.handle, ctypes.cast(xbuf, _vp), _dev_ptr(y_dev), n,
+                         _dev_ptr(pos_dev), int(cap), ctypes.byref(cnt), _stream_handle(stream))
+    if not (allow_truncated and rc == HC_ERR_CAPACITY):
+        _check(rc, "hc_search")
     return cnt.value
 
 
@@ -210,7 +244,7 @@ def search_positions(f: HCFilter, x, y_dev, stream=None):
     """All occurrence positions of x in y_dev as an int64 CUDA tensor: one
     counting call (cap = 0), then one call into a buffer of that size."""
     import torch
-    count = hc_search(f, x, y_dev, None, 0, stream)
+    count = hc_search(f, x, y_dev, None, 0, stream, allow_truncated=True)
     pos = torch.empty(max(count, 1), dtype=torch.int64, device=y_dev.device)
     count2 = hc_search(f, x, y_dev, pos, count, stream)
     assert count2 == count

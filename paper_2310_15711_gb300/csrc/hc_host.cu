@@ -56,6 +56,27 @@ const DeviceInfo& device_info(int dev) {
   return g_dev_info.emplace(dev, di).first->second;
 }
 
+cudaMemPool_t device_pool(int dev) {
+  static std::mutex mu;
+  static std::unordered_map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    cudaDeviceGetDefaultMemPool(&pool, dev);
+  }
+  uint64_t keep = ~0ull;  // never hand freed memory back to the driver
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools.emplace(dev, pool);
+  return pool;
+}
+
 int filter_to_device(Filter* f) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -59,4 +59,29 @@ struct DeviceInfo {
 };
 const DeviceInfo& device_info(int dev);
 
+// The library's stream-ordered memory pool of a device (workspaces); it keeps
+// freed memory for reuse instead of returning it to the driver.
+cudaMemPool_t device_pool(int dev);
+
+// Launch shape of one search (two kernels: scan, emit) and its workspace.
+struct SearchArgs;
+using KernelFn = void (*)(const SearchArgs);
+struct SearchPlan {
+  int kind = HC_MODE_STAGED;      // HC_MODE_STAGED, HC_MODE_DIRECT or HC_MODE_DENSE
+  int L = 0;                      // window starts per thread
+  uint32_t C = 0;                 // window starts per chunk
+  int stages = 0;                 // staging buffers per CTA
+  uint32_t stage_bytes = 0, x_smem = 0;
+  size_t smem_scan = 0, smem_emit = 0;
+  KernelFn scan = nullptr, emit = nullptr;
+  unsigned long long num_chunks = 0, chunks_per_cta = 0, grid = 0, region_entries = 0;
+  size_t ws_bytes = 0;            // workspace bytes (device), no zeroing needed
+};
+
+int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, int dev,
+                SearchPlan* out);
+int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
+                   uint64_t* pos, size_t cap, uint64_t* count_dev, void* ws,
+                   cudaStream_t stream);
+
 }  // namespace hc

@@ -2,12 +2,13 @@
 // early reject of Sec. 3.4) on sm_103a.
 //
 // Decomposition.  The window starts [0, n-m] are cut into chunks of C = 256*L
-// consecutive starts; chunk k reads text bytes [kC, kC + C + m - 1).  A
-// persistent grid of CTAs claims chunks in increasing order from an atomic
-// counter.  Each CTA keeps F (2^alpha words) and x in shared memory and
-// double-buffers its chunks: while it scans one chunk, the next one is
-// already in flight from HBM into shared memory as a 1-D bulk copy (TMA,
-// cp.async.bulk, 16-byte aligned) completing on an mbarrier.
+// consecutive starts; chunk k reads text bytes [kC, kC + C + m - 1).  A grid
+// sized to fill the GPU (a whole number of CTAs per SM) gives each CTA a
+// contiguous range of chunks.  Each CTA keeps F (2^alpha words) and x in
+// shared memory and streams its chunks through 2-4 staging buffers: while it
+// scans one chunk, the next ones are in flight from HBM into shared memory as
+// 1-D bulk copies (TMA, cp.async.bulk, 16-byte aligned) completing on
+// mbarriers.
 //
 // Inside a chunk, thread t runs the sequential HC loop over its own L window
 // starts [tL, tL + L).  This is exact: HC started at any window reports every
@@ -17,21 +18,24 @@
 // so the 32 lanes of a warp, whose windows advance in step while they miss,
 // read 32 different shared-memory banks.
 //
-// Output in text order.  Each thread counts its occurrences (keeping the
-// first four in shared memory); a block scan gives each thread's offset in
-// the chunk and the chunk total; a single-pass decoupled look-back over the
-// per-chunk states (aggregate / inclusive prefix) gives the chunk's offset
-// in the output; threads then write their positions (threads with more than
-// four re-scan their segment from shared memory to write the rest).  Chunk
-// 0's inclusive prefix needs no look-back, so the chain always resolves.
+// Output in text order, without any wait between CTAs.  CTA b scans a
+// contiguous range of chunks.  Per chunk, each thread counts its occurrences
+// (keeping the first four in shared memory); when a chunk has any, a block
+// scan orders them and they are appended, in text order, to CTA b's private
+// spill region in global memory (as offsets from the start of its range).
+// A second, light kernel gives CTA b its output offset (the sum of the
+// totals of CTAs 0..b-1) and copies its region to the output.  A region that
+// fills up is marked at the first chunk that did not fit; the second kernel
+// re-scans the text from that chunk on and writes those positions itself.
 //
-// Every wait (bulk-copy completion, a predecessor chunk's state) is bounded;
-// a wait that gives up sets the status flag and the kernel returns.
+// Every wait (bulk-copy completion) is bounded; a wait that gives up sets
+// the status flag and the kernel returns.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
-#include <set>
+#include <map>
+#include <tuple>
 #include <utility>
 
 #include "hc_device.cuh"
@@ -41,13 +45,12 @@ namespace hc {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kStages = 2;
+constexpr int kMaxStages = 4;
 constexpr int kSlots = 4;
 constexpr int kMaxSmemX = 4096;             // larger patterns verify from global memory
 constexpr size_t kMaxStagedM = 16384;       // larger patterns use the unstaged kernel
-constexpr unsigned long long kFlagAgg = 1ull << 62;
-constexpr unsigned long long kFlagInc = 2ull << 62;
-constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr unsigned long long kNoOverflow = ~0ull;
+constexpr int kDirectShift = 200;           // shifts this long skip most 32-byte sectors
 
 // bit 0: a bounded device-side wait gave up
 __device__ unsigned int g_status;
@@ -64,45 +67,79 @@ struct SearchArgs {
   unsigned long long* pos;   // output positions (device), cap of them
   unsigned long long cap;
   unsigned long long* count_out;
-  unsigned long long* state; // per-chunk look-back state, zeroed
-  unsigned long long* claim; // chunk claim counter, zeroed
+  // workspace (no zeroing needed: the scan kernel writes every entry it or
+  // the emit kernel reads)
+  unsigned long long* cta_total;     // [grid] occurrences in CTA b's range
+  unsigned long long* cta_overflow;  // [grid] (first unstored chunk << 40) | stored, or kNoOverflow
+  uint32_t* region;                  // [grid * region_entries] offsets from range start
+  unsigned long long region_entries;
   unsigned long long num_chunks;
+  unsigned long long chunks_per_cta;
   int L;                     // window starts per thread
   uint32_t C;                // window starts per chunk (kThreads * L)
   int head;                  // y mod 16: offset of y[kC] in its staged buffer
   uint32_t stage_bytes;      // bytes per staging buffer (16-byte multiple)
   uint32_t x_smem;           // bytes of shared memory for x (0: verify from global)
+  int stages;                // staging buffers per CTA (2..kMaxStages)
+  // h as at most two byte-dot-products (see qgram_hash): bytes [0, g0) with
+  // weights w0, bytes [g0, q) with weights w1, scaled by 2^(s*g0)
+  uint32_t w0, w1;
+  int g0;
 };
 
 // ---------------------------------------------------------------------------
-// q-gram hash h (Eq. 3, Eq. 4): the q bytes starting at byte offset o of
-// `base`, weight 2^(s*k) for the k-th byte, mod 2^alpha.  Evaluated by
-// Horner's rule from the last byte down, as in the paper's Hash routine.
-// Staged: `base` is a 16-byte aligned shared-memory buffer with at least 12
-// readable bytes past the q-gram; the bytes come from two or three aligned
-// 32-bit loads and funnel shifts.  Unstaged: byte loads from global memory.
+// q-gram hash h (Eq. 3, Eq. 4): sum over the q bytes b_k (first byte k = 0)
+// of b_k * 2^(s*k), mod 2^alpha.  The bytes are split into at most two
+// groups, [0, g0) and [g0, q), chosen on the host so that every weight
+// 2^(s*k) inside a group fits in one byte; each group is then one unsigned
+// 4-byte dot product (dp4a), and h = dot0 + (dot1 << (s*g0)).  With
+// alpha <= 15 and q <= 8 two groups always suffice (s*(q-1) <= 7 for q >= 4
+// or a split after 2-4 bytes), and the value equals the Horner evaluation of
+// Eq. 3 exactly, since no partial sum exceeds 32 bits.
+// `lo` holds bytes 0-3 of the q-gram, `hi` bytes 4-7 (little-endian).
+template <int Q>
+__device__ __forceinline__ uint32_t hash_bytes(uint32_t lo, uint32_t hi, const SearchArgs& a) {
+  uint32_t v = __dp4a(lo, a.w0, 0u);
+  if constexpr (Q > 1) {
+    if (Q > a.g0) {
+      const uint32_t rest = __funnelshift_rc(lo, hi, 8u * static_cast<uint32_t>(a.g0));
+      v += __dp4a(rest, a.w1, 0u) << (a.s * a.g0);
+    }
+  }
+  return v & a.mask;
+}
+
+// The q bytes starting at byte offset o of `base`: staged -- `base` is a
+// 16-byte aligned shared-memory buffer with at least 12 readable bytes past
+// the q-gram, read as aligned 32-bit words and funnel-shifted; unstaged --
+// byte loads from global memory (no read outside the q-gram).
 template <int Q, bool STAGED>
-__device__ __forceinline__ uint32_t qgram_hash(const uint8_t* base, int o, int s,
-                                               uint32_t mask) {
-  uint32_t v = 0;
+__device__ __forceinline__ void load_qgram(const uint8_t* base, int o, uint32_t* lo, uint32_t* hi) {
   if constexpr (STAGED) {
     const uint32_t* W = reinterpret_cast<const uint32_t*>(base);
     const int wi = o >> 2;
     const uint32_t r = static_cast<uint32_t>(o & 3) * 8u;
     const uint32_t w0 = W[wi], w1 = W[wi + 1];
-    const uint32_t lo = __funnelshift_r(w0, w1, r);
-    uint32_t hi = 0;
-    if constexpr (Q > 4) hi = __funnelshift_r(w1, W[wi + 2], r);
-#pragma unroll
-    for (int k = Q - 1; k >= 0; --k) {
-      const uint32_t b = (k < 4) ? ((lo >> (8 * k)) & 0xffu) : ((hi >> (8 * (k - 4))) & 0xffu);
-      v = (v << s) + b;
-    }
+    *lo = __funnelshift_r(w0, w1, r);
+    *hi = 0;
+    if constexpr (Q > 4) *hi = __funnelshift_r(w1, W[wi + 2], r);
   } else {
+    uint32_t l = 0, h = 0;
 #pragma unroll
-    for (int k = Q - 1; k >= 0; --k) v = (v << s) + static_cast<uint32_t>(__ldg(base + o + k));
+    for (int k = 0; k < Q; ++k) {
+      const uint32_t b = __ldg(base + o + k);
+      if (k < 4) l |= b << (8 * k); else h |= b << (8 * (k - 4));
+    }
+    *lo = l;
+    *hi = h;
   }
-  return v & mask;
+}
+
+template <int Q, bool STAGED>
+__device__ __forceinline__ uint32_t qgram_hash(const uint8_t* base, int o, const SearchArgs& a) {
+  uint32_t lo, hi;
+  load_qgram<Q, STAGED>(base, o, &lo, &hi);
+  return hash_bytes<Q>(lo, hi, a);
 }
 
 __device__ __forceinline__ bool verify_window(const uint8_t* w, const uint8_t* x, int m) {
@@ -111,25 +148,32 @@ __device__ __forceinline__ bool verify_window(const uint8_t* w, const uint8_t* x
   return true;
 }
 
+enum SinkMode { kCount = 0, kToRegion = 1, kToPositions = 2 };
+
+// Where a segment scan puts the occurrences it finds.
+struct Sink {
+  uint32_t* slot;            // kCount: first kSlots starts at slot[k * kThreads]
+  uint32_t* region;          // kToRegion: region[obase + i] = vbase + start
+  unsigned long long* pos;   // kToPositions: pos[obase + i] = vbase + start
+  unsigned long long obase, vbase, limit;
+};
+
 // Sequential HC (Fig. 5 left) over the window starts [lo, hi) of a chunk.
-// Chunk-relative text byte k is base[head + k].  Counts the occurrences;
-// without WRITE the first kSlots starts go to slot[0], slot[kThreads], ...;
-// with WRITE every occurrence is written to pos[obase + i] (if below cap).
-template <int Q, bool STAGED, bool WRITE>
+// Chunk-relative text byte k is base[head + k].  Returns the number of
+// occurrences found; stores them according to MODE.
+template <int Q, bool STAGED, int MODE>
 __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int lo, int hi,
                                             const SearchArgs& a, const uint32_t* Fs,
-                                            const uint8_t* xv, uint32_t* slot,
-                                            unsigned long long obase,
-                                            unsigned long long chunk_start) {
-  const int m = a.m, s = a.s;
-  const uint32_t mask = a.mask, hv = a.hv;
+                                            const uint8_t* xv, const Sink& sink) {
+  const int m = a.m;
+  const uint32_t hv = a.hv;
   const int shift = m - Q + 1;
   int cnt = 0;
   int e = lo + m - 1;              // window end (chunk-relative)
   const int e_end = hi + m - 1;    // first window end past the segment
   while (e < e_end) {
     // first test: the q-gram ending at the window end
-    uint32_t v = qgram_hash<Q, STAGED>(base, head + e - Q + 1, s, mask);
+    uint32_t v = qgram_hash<Q, STAGED>(base, head + e - Q + 1, a);
     uint32_t z = Fs[v];
     if (z == 0) {
       e += shift;
@@ -141,7 +185,7 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
     bool full = true;
     while (j >= i) {
       j -= Q;
-      v = qgram_hash<Q, STAGED>(base, head + j - Q + 1, s, mask);
+      v = qgram_hash<Q, STAGED>(base, head + j - Q + 1, a);
       if ((z & (1u << (v & 31u))) == 0) {
         full = false;
         break;
@@ -154,11 +198,16 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
     }
     const int start = e - m + 1;
     if (v == hv && verify_window(base + head + start, xv, m)) {
-      if constexpr (WRITE) {
-        const unsigned long long idx = obase + static_cast<unsigned long long>(cnt);
-        if (idx < a.cap) a.pos[idx] = chunk_start + static_cast<unsigned long long>(start);
+      if constexpr (MODE == kCount) {
+        if (cnt < kSlots) sink.slot[cnt * kThreads] = static_cast<uint32_t>(start);
       } else {
-        if (cnt < kSlots) slot[cnt * kThreads] = static_cast<uint32_t>(start);
+        const unsigned long long idx = sink.obase + static_cast<unsigned long long>(cnt);
+        if (idx < sink.limit) {
+          if constexpr (MODE == kToRegion)
+            sink.region[idx] = static_cast<uint32_t>(sink.vbase + static_cast<unsigned>(start));
+          else
+            sink.pos[idx] = sink.vbase + static_cast<unsigned long long>(start);
+        }
       }
       ++cnt;
     }
@@ -167,48 +216,28 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
   return cnt;
 }
 
-// Decoupled look-back by one warp: publishes chunk c's aggregate, sums the
-// predecessors' values back to the nearest inclusive prefix, publishes c's
-// inclusive prefix.  Returns false if a wait gave up.
-__device__ bool chunk_lookback(const SearchArgs& a, long long c, unsigned long long total,
-                               unsigned long long* excl_out) {
-  const int lane = threadIdx.x & 31;
-  if (c == 0) {
-    if (lane == 0) st_relaxed_u64(&a.state[0], kFlagInc | total);
-    *excl_out = 0;
-    return true;
+// Block-wide exclusive scan of one count per thread; every thread gets its
+// exclusive prefix and the block total.  Uses warp_sum (kWarps words).
+__device__ __forceinline__ void block_scan(uint32_t cnt, uint32_t* warp_sum, uint32_t* excl,
+                                           uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t incl = warp_incl_scan_u32(cnt);
+  if (lane == 31) warp_sum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kWarps ? warp_sum[lane] : 0u;
+    w = warp_incl_scan_u32(w);
+    if (lane < kWarps) warp_sum[lane] = w;
   }
-  if (lane == 0) st_relaxed_u64(&a.state[c], kFlagAgg | total);
-  unsigned long long excl = 0;
-  long long base = c - 1;
-  const uint64_t t0 = global_timer_ns();
-  while (true) {
-    const long long idx = base - lane;
-    unsigned long long v = kFlagInc;  // before chunk 0: inclusive prefix 0
-    if (idx >= 0) {
-      v = ld_relaxed_u64(&a.state[idx]);
-      for (uint32_t spins = 0; (v >> 62) == 0 && spins < kMaxSpins; ++spins) {
-        if ((spins & 63u) == 63u && global_timer_ns() - t0 > kWaitLimitNs) break;
-        __nanosleep(64);
-        v = ld_relaxed_u64(&a.state[idx]);
-      }
-    }
-    if (__any_sync(0xffffffffu, (v >> 62) == 0)) return false;
-    const unsigned inc = __ballot_sync(0xffffffffu, (v >> 62) == 2);
-    const int stop = inc ? (__ffs(inc) - 1) : 31;
-    excl += warp_sum_u64(lane <= stop ? (v & kValMask) : 0ull);
-    if (inc) break;
-    base -= 32;
-  }
-  if (lane == 0) st_relaxed_u64(&a.state[c], kFlagInc | (excl + total));
-  *excl_out = excl;
-  return true;
+  __syncthreads();
+  *excl = (warp ? warp_sum[warp - 1] : 0u) + incl - cnt;
+  *total = warp_sum[kWarps - 1];
 }
 
 // Starts the bulk copy of chunk c's text into staging buffer `st`.
 __device__ __forceinline__ void issue_chunk(const SearchArgs& a, uint8_t* stages, uint64_t* bars,
-                                            int st, long long c) {
-  const unsigned long long cs = static_cast<unsigned long long>(c) * a.C;
+                                            int st, unsigned long long c) {
+  const unsigned long long cs = c * a.C;
   const unsigned long long len = min(static_cast<unsigned long long>(a.C) + a.m - 1, a.n - cs);
   const uint32_t bytes = static_cast<uint32_t>((a.head + len + 15) & ~15ull);
   const uint8_t* src = a.y + cs - a.head;  // 16-byte aligned: C is a multiple of 16
@@ -216,71 +245,71 @@ __device__ __forceinline__ void issue_chunk(const SearchArgs& a, uint8_t* stages
   bulk_copy_g2s(stages + static_cast<size_t>(st) * a.stage_bytes, src, bytes, &bars[st]);
 }
 
+// ---------------------------------------------------------------------------
+// Kernel 1: HC over CTA b's contiguous range of chunks; occurrences go to
+// b's spill region in text order; the total to cta_total[b].
 template <int Q, bool STAGED>
-__global__ void __launch_bounds__(kThreads) hc_search_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(kThreads) hc_scan_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[kStages];
-  __shared__ long long chunk_id[kStages];
+  __shared__ __align__(8) uint64_t bars[kMaxStages];
   __shared__ uint32_t warp_sum[kWarps];
-  __shared__ unsigned long long s_excl;
   __shared__ int s_abort;
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
+  const unsigned long long b = blockIdx.x;
+  const unsigned long long c0 = b * a.chunks_per_cta;
+  const unsigned long long c1 = min(c0 + a.chunks_per_cta, a.num_chunks);
+  if (c0 >= c1) {
+    if (tid == 0) {
+      a.cta_total[b] = 0;
+      a.cta_overflow[b] = kNoOverflow;
+    }
+    return;
+  }
   uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
   const uint32_t f_bytes = (a.fwords * 4u + 15u) & ~15u;
   uint8_t* xs = smem + f_bytes;
   uint8_t* stages = xs + a.x_smem;
-  uint32_t* slots = reinterpret_cast<uint32_t*>(stages + (STAGED ? kStages * a.stage_bytes : 0u));
+  uint32_t* slots =
+      reinterpret_cast<uint32_t*>(stages + (STAGED ? a.stages * a.stage_bytes : 0u));
+  const int nchunks = static_cast<int>(c1 - c0);
+  const int nst = a.stages;
 
+  if (tid == 0) {
+    s_abort = 0;
+    if constexpr (STAGED) {
+      for (int k = 0; k < nst; ++k) mbar_init(&bars[k], 1);
+      fence_mbar_init();
+      for (int k = 0; k < nst && k < nchunks; ++k) issue_chunk(a, stages, bars, k, c0 + k);
+    }
+  }
   for (uint32_t i = tid; i < a.fwords; i += kThreads) Fs[i] = a.F[i];
   for (uint32_t i = tid; i < a.x_smem && i < static_cast<uint32_t>(a.m); i += kThreads)
     xs[i] = a.x[i];
   const uint8_t* xv = a.x_smem ? xs : a.x;
-
-  uint32_t inflight = 0;  // thread 0: bit st set while stage st has a copy in flight
-  if (tid == 0) {
-    s_abort = 0;
-    const long long c = static_cast<long long>(atomicAdd(a.claim, 1ull));
-    chunk_id[0] = c;
-    if constexpr (STAGED) {
-      for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
-      fence_mbar_init();
-      if (c < static_cast<long long>(a.num_chunks)) {
-        issue_chunk(a, stages, bars, 0, c);
-        inflight |= 1u;
-      }
-    }
-  }
   __syncthreads();
 
-  uint32_t parity = 0;  // bit st: parity of the next completion of stage st
-  int st = 0;
-  for (;; st ^= 1) {
-    const long long c = chunk_id[st];
-    if (c >= static_cast<long long>(a.num_chunks)) break;
-    if (tid == 0) {  // claim (and prefetch) the next chunk
-      const long long cn = static_cast<long long>(atomicAdd(a.claim, 1ull));
-      chunk_id[st ^ 1] = cn;
-      if constexpr (STAGED) {
-        if (cn < static_cast<long long>(a.num_chunks)) {
-          fence_proxy_async_smem();
-          issue_chunk(a, stages, bars, st ^ 1, cn);
-          inflight |= 2u >> st;
-        }
-      }
-    }
+  const unsigned long long S = a.region_entries;
+  uint32_t* region = a.region + b * S;
+  unsigned long long T = 0;               // occurrences so far in this range
+  unsigned long long overflow = kNoOverflow;
+  Sink sink{};
+  sink.slot = slots + tid;
+  int i = 0;
+  for (; i < nchunks; ++i) {
+    const int st = i % nst;
+    const unsigned long long c = c0 + static_cast<unsigned long long>(i);
+    bool ok = true;
     if constexpr (STAGED) {
-      if (mbar_wait_bounded(&bars[st], (parity >> st) & 1u)) {
-        parity ^= 1u << st;
-        inflight &= ~(1u << st);
-      } else {
-        s_abort = 1;
+      if (tid == 0 && i > 0 && i + nst - 1 < nchunks) {
+        // the buffer of chunk i-1 was released by the barrier that ended it
+        fence_proxy_async_smem();
+        issue_chunk(a, stages, bars, (i + nst - 1) % nst, c + nst - 1);
       }
-      __syncthreads();
-      if (s_abort) break;
+      ok = mbar_wait_bounded(&bars[st], static_cast<uint32_t>(i / nst) & 1u);
+      if (!ok) s_abort = 1;
     }
-
-    const unsigned long long cs = static_cast<unsigned long long>(c) * a.C;
+    const unsigned long long cs = c * a.C;
     const int wins = static_cast<int>(min(static_cast<unsigned long long>(a.C), a.nwin - cs));
     const uint8_t* base;
     int head;
@@ -293,55 +322,258 @@ __global__ void __launch_bounds__(kThreads) hc_search_kernel(const SearchArgs a)
     }
     const int lo = tid * a.L;
     const int hi = min(lo + a.L, wins);
-    uint32_t* my_slot = slots + tid;
     int cnt = 0;
-    if (lo < hi)
-      cnt = scan_segment<Q, STAGED, false>(base, head, lo, hi, a, Fs, xv, my_slot, 0, 0);
+    if (ok && lo < hi) cnt = scan_segment<Q, STAGED, kCount>(base, head, lo, hi, a, Fs, xv, sink);
 
-    // block-wide exclusive scan of the per-thread counts
-    const uint32_t incl = warp_incl_scan_u32(static_cast<uint32_t>(cnt));
-    if (lane == 31) warp_sum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = lane < kWarps ? warp_sum[lane] : 0u;
-      w = warp_incl_scan_u32(w);
-      if (lane < kWarps) warp_sum[lane] = w;
-    }
-    __syncthreads();
-    const uint32_t thread_excl = (warp ? warp_sum[warp - 1] : 0u) + incl - static_cast<uint32_t>(cnt);
-    const uint32_t total = warp_sum[kWarps - 1];
-    if (warp == 0) {
-      unsigned long long ex = 0;
-      const bool ok = chunk_lookback(a, c, total, &ex);
-      if (lane == 0) {
-        s_excl = ex;
-        if (!ok) s_abort = 1;
-        else if (c == static_cast<long long>(a.num_chunks) - 1) *a.count_out = ex + total;
-      }
-    }
-    __syncthreads();
+    // one barrier per chunk in the common case (no occurrence in the chunk)
+    if (!__syncthreads_or(cnt != 0 || !ok)) continue;
     if (s_abort) break;
-    if (cnt > 0) {
-      const unsigned long long ob = s_excl + thread_excl;
-      if (cnt <= kSlots) {
-        for (int k = 0; k < cnt; ++k) {
-          const unsigned long long idx = ob + static_cast<unsigned long long>(k);
-          if (idx < a.cap) a.pos[idx] = cs + my_slot[k * kThreads];
+    uint32_t excl, total;
+    block_scan(static_cast<uint32_t>(cnt), warp_sum, &excl, &total);
+    if (overflow == kNoOverflow) {
+      if (T + total <= S) {
+        const uint32_t rel = static_cast<uint32_t>(static_cast<unsigned long long>(i) * a.C);
+        const unsigned long long ob = T + excl;
+        if (cnt <= kSlots) {
+          for (int k = 0; k < cnt; ++k) region[ob + k] = rel + sink.slot[k * kThreads];
+        } else {
+          Sink w{};
+          w.region = region;
+          w.obase = ob;
+          w.vbase = rel;
+          w.limit = S;
+          scan_segment<Q, STAGED, kToRegion>(base, head, lo, hi, a, Fs, xv, w);
         }
       } else {
-        scan_segment<Q, STAGED, true>(base, head, lo, hi, a, Fs, xv, nullptr, ob, cs);
+        overflow = (static_cast<unsigned long long>(i) << 40) | T;
       }
     }
-    __syncthreads();  // staging buffer st and the scan scratch are free again
+    T += total;
+    __syncthreads();  // staging buffer, slots and warp_sum are free again
   }
 
-  if (s_abort && tid == 0) {
-    atomicOr(&g_status, 1u);
-    if constexpr (STAGED) {
-      // let copies still in flight land before the CTA's shared memory goes
-      for (int k = 0; k < kStages; ++k)
-        if (inflight & (1u << k)) (void)mbar_wait_bounded(&bars[k], (parity >> k) & 1u);
+  if (tid == 0) {
+    a.cta_total[b] = T;
+    a.cta_overflow[b] = overflow;
+    if (s_abort) {
+      atomicOr(&g_status, 1u);
+      if constexpr (STAGED) {
+        // let the copies still in flight land before the CTA's shared memory goes
+        for (int j = i; j < nchunks && j < i + nst; ++j)
+          (void)mbar_wait_bounded(&bars[j % nst], static_cast<uint32_t>(j / nst) & 1u);
+      }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 1, dense form for m = q.  With m = q the window is a single q-gram,
+// the back-walk is empty and every shift is one position, so HC tests every
+// window in turn: first test F[h] != 0, then h = H_v, then the byte
+// comparison.  Here the 32 lanes of a warp test 32 consecutive windows at
+// once (warp w owns a contiguous slice of the chunk), and the warp compacts
+// its matches in order with a ballot into a shared-memory list; a scan over
+// the warps appends the chunk's matches to the CTA's spill region.
+template <int Q>
+__global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bars[kMaxStages];
+  __shared__ uint32_t warp_cnt[kWarps];
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned long long b = blockIdx.x;
+  const unsigned long long c0 = b * a.chunks_per_cta;
+  const unsigned long long c1 = min(c0 + a.chunks_per_cta, a.num_chunks);
+  if (c0 >= c1) {
+    if (tid == 0) {
+      a.cta_total[b] = 0;
+      a.cta_overflow[b] = kNoOverflow;
+    }
+    return;
+  }
+  uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
+  const uint32_t f_bytes = (a.fwords * 4u + 15u) & ~15u;
+  uint8_t* stages = smem + f_bytes;
+  const uint32_t wslice = a.C / kWarps;  // windows per warp and chunk
+  uint16_t* wlist = reinterpret_cast<uint16_t*>(stages + a.stages * a.stage_bytes) + warp * wslice;
+  const int nchunks = static_cast<int>(c1 - c0);
+  const int nst = a.stages;
+
+  if (tid == 0) {
+    s_abort = 0;
+    for (int k = 0; k < nst; ++k) mbar_init(&bars[k], 1);
+    fence_mbar_init();
+    for (int k = 0; k < nst && k < nchunks; ++k) issue_chunk(a, stages, bars, k, c0 + k);
+  }
+  for (uint32_t i = tid; i < a.fwords; i += kThreads) Fs[i] = a.F[i];
+  // the pattern, packed like the text words below, and the mask of its Q bytes
+  uint32_t xlo = 0, xhi = 0;
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const uint32_t xb = a.x[k];
+    if (k < 4) xlo |= xb << (8 * k); else xhi |= xb << (8 * (k - 4));
+  }
+  const uint32_t mlo = Q >= 4 ? 0xffffffffu : ((1u << (8 * Q)) - 1u);
+  const uint32_t mhi = Q >= 8 ? 0xffffffffu : (Q > 4 ? ((1u << (8 * (Q - 4))) - 1u) : 0u);
+  uint32_t lt_mask;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt_mask));
+  __syncthreads();
+
+  const unsigned long long S = a.region_entries;
+  uint32_t* region = a.region + b * S;
+  unsigned long long T = 0;
+  unsigned long long overflow = kNoOverflow;
+  const uint32_t hv = a.hv;
+  int i = 0;
+  for (; i < nchunks; ++i) {
+    const int st = i % nst;
+    const unsigned long long c = c0 + static_cast<unsigned long long>(i);
+    if (tid == 0 && i > 0 && i + nst - 1 < nchunks) {
+      fence_proxy_async_smem();
+      issue_chunk(a, stages, bars, (i + nst - 1) % nst, c + nst - 1);
+    }
+    const bool ok = mbar_wait_bounded(&bars[st], static_cast<uint32_t>(i / nst) & 1u);
+    if (!ok) s_abort = 1;
+    const unsigned long long cs = c * a.C;
+    const uint32_t wins = static_cast<uint32_t>(min(static_cast<unsigned long long>(a.C), a.nwin - cs));
+    const uint32_t* W = reinterpret_cast<const uint32_t*>(stages + static_cast<size_t>(st) * a.stage_bytes);
+    const uint32_t w_lo = warp * wslice;
+    const uint32_t w_hi = min(w_lo + wslice, wins);
+    uint32_t cnt = 0;
+    if (ok) {
+      for (uint32_t base = w_lo; base < w_hi; base += 32) {
+        const uint32_t start = base + lane;
+        const uint32_t o = static_cast<uint32_t>(a.head) + start;
+        const uint32_t r = (o & 3u) * 8u;
+        const uint32_t w0 = W[o >> 2], w1 = W[(o >> 2) + 1];
+        const uint32_t lo = __funnelshift_r(w0, w1, r);
+        uint32_t hi = 0;
+        if constexpr (Q > 4) hi = __funnelshift_r(w1, W[(o >> 2) + 2], r);
+        const uint32_t v = hash_bytes<Q>(lo, hi, a);
+        const bool match = start < w_hi && Fs[v] != 0u && v == hv &&
+                           ((lo ^ xlo) & mlo) == 0u && ((hi ^ xhi) & mhi) == 0u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, match);
+        if (match) wlist[cnt + __popc(bal & lt_mask)] = static_cast<uint16_t>(start);
+        cnt += __popc(bal);
+      }
+    }
+    if (!__syncthreads_or(cnt != 0u || !ok)) continue;
+    if (s_abort) break;
+    if (lane == 0) warp_cnt[warp] = cnt;
+    __syncthreads();
+    uint32_t excl = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t cw = warp_cnt[w];
+      excl += w < warp ? cw : 0u;
+      total += cw;
+    }
+    if (overflow == kNoOverflow) {
+      if (T + total <= S) {
+        const uint32_t rel = static_cast<uint32_t>(static_cast<unsigned long long>(i) * a.C);
+        for (uint32_t k = lane; k < cnt; k += 32) region[T + excl + k] = rel + wlist[k];
+      } else {
+        overflow = (static_cast<unsigned long long>(i) << 40) | T;
+      }
+    }
+    T += total;
+    __syncthreads();  // staging buffer, lists and counts are free again
+  }
+
+  if (tid == 0) {
+    a.cta_total[b] = T;
+    a.cta_overflow[b] = overflow;
+    if (s_abort) {
+      atomicOr(&g_status, 1u);
+      for (int j = i; j < nchunks && j < i + nst; ++j)
+        (void)mbar_wait_bounded(&bars[j % nst], static_cast<uint32_t>(j / nst) & 1u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 2: CTA b's output offset is the sum of cta_total[0..b); copy b's
+// region to the output; re-scan (from global memory) the chunks whose
+// occurrences did not fit in the region.  The last CTA writes the count.
+template <int Q>
+__global__ void __launch_bounds__(kThreads) hc_emit_kernel(const SearchArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ unsigned long long red[kWarps];
+  __shared__ uint32_t warp_sum[kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned long long b = blockIdx.x;
+
+  unsigned long long p = 0;
+  for (unsigned long long k = tid; k < b; k += kThreads) p += a.cta_total[k];
+  p = warp_sum_u64(p);
+  if (lane == 0) red[warp] = p;
+  __syncthreads();
+  unsigned long long P = 0;
+  for (int w = 0; w < kWarps; ++w) P += red[w];
+
+  const unsigned long long T = a.cta_total[b];
+  const unsigned long long ovf = a.cta_overflow[b];
+  const unsigned long long stored = ovf == kNoOverflow ? T : (ovf & ((1ull << 40) - 1));
+  const unsigned long long c0 = b * a.chunks_per_cta;
+  const unsigned long long vbase = c0 * a.C;
+  const uint32_t* region = a.region + b * a.region_entries;
+  // copy: 16-byte region loads (regions are 16-byte aligned), four of them
+  // in flight per thread
+  const unsigned long long ncopy = a.cap > P ? min(stored, a.cap - P) : 0ull;
+  const uint4* r4 = reinterpret_cast<const uint4*>(region);
+  const unsigned long long nvec = (ncopy + 3) / 4;
+  for (unsigned long long k0 = tid; k0 < nvec; k0 += 4ull * kThreads) {
+    uint4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned long long k = k0 + static_cast<unsigned long long>(u) * kThreads;
+      if (k < nvec) v[u] = __ldcs(r4 + k);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned long long k = (k0 + static_cast<unsigned long long>(u) * kThreads) * 4;
+      if (k < ncopy) {
+        unsigned long long* o = a.pos + P + k;
+        __stcs(o, vbase + v[u].x);
+        if (k + 1 < ncopy) __stcs(o + 1, vbase + v[u].y);
+        if (k + 2 < ncopy) __stcs(o + 2, vbase + v[u].z);
+        if (k + 3 < ncopy) __stcs(o + 3, vbase + v[u].w);
+      }
+    }
+  }
+  if (b == gridDim.x - 1 && tid == 0) *a.count_out = P + T;
+  if (ovf == kNoOverflow || P + stored >= a.cap) return;
+
+  // re-scan the chunks from the first unstored one on
+  uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* slots = Fs + ((a.fwords + 3u) & ~3u);
+  for (uint32_t k = tid; k < a.fwords; k += kThreads) Fs[k] = a.F[k];
+  __syncthreads();
+  const unsigned long long c1 = min(c0 + a.chunks_per_cta, a.num_chunks);
+  unsigned long long out = P + stored;
+  Sink cs_sink{};
+  cs_sink.slot = slots + tid;
+  for (unsigned long long c = c0 + (ovf >> 40); c < c1 && out < a.cap; ++c) {
+    const unsigned long long cs = c * a.C;
+    const int wins = static_cast<int>(min(static_cast<unsigned long long>(a.C), a.nwin - cs));
+    const int lo = tid * a.L;
+    const int hi = min(lo + a.L, wins);
+    const uint8_t* base = a.y + cs;
+    int cnt = 0;
+    if (lo < hi) cnt = scan_segment<Q, false, kCount>(base, 0, lo, hi, a, Fs, a.x, cs_sink);
+    uint32_t excl, total;
+    block_scan(static_cast<uint32_t>(cnt), warp_sum, &excl, &total);
+    if (cnt > 0) {
+      Sink w{};
+      w.pos = a.pos;
+      w.obase = out + excl;
+      w.vbase = cs;
+      w.limit = a.cap;
+      scan_segment<Q, false, kToPositions>(base, 0, lo, hi, a, Fs, a.x, w);
+    }
+    out += total;
+    __syncthreads();
   }
 }
 
@@ -349,110 +581,200 @@ __global__ void __launch_bounds__(kThreads) hc_search_kernel(const SearchArgs a)
 // host side
 namespace {
 
-using KernelFn = void (*)(const SearchArgs);
-
 template <bool STAGED>
-KernelFn kernel_for_q(int q) {
+KernelFn scan_kernel_for_q(int q) {
   switch (q) {
-    case 1: return hc_search_kernel<1, STAGED>;
-    case 2: return hc_search_kernel<2, STAGED>;
-    case 3: return hc_search_kernel<3, STAGED>;
-    case 4: return hc_search_kernel<4, STAGED>;
-    case 5: return hc_search_kernel<5, STAGED>;
-    case 6: return hc_search_kernel<6, STAGED>;
-    case 7: return hc_search_kernel<7, STAGED>;
-    default: return hc_search_kernel<8, STAGED>;
+    case 1: return hc_scan_kernel<1, STAGED>;
+    case 2: return hc_scan_kernel<2, STAGED>;
+    case 3: return hc_scan_kernel<3, STAGED>;
+    case 4: return hc_scan_kernel<4, STAGED>;
+    case 5: return hc_scan_kernel<5, STAGED>;
+    case 6: return hc_scan_kernel<6, STAGED>;
+    case 7: return hc_scan_kernel<7, STAGED>;
+    default: return hc_scan_kernel<8, STAGED>;
+  }
+}
+
+KernelFn dense_kernel_for_q(int q) {
+  switch (q) {
+    case 1: return hc_scan_dense_kernel<1>;
+    case 2: return hc_scan_dense_kernel<2>;
+    case 3: return hc_scan_dense_kernel<3>;
+    case 4: return hc_scan_dense_kernel<4>;
+    case 5: return hc_scan_dense_kernel<5>;
+    case 6: return hc_scan_dense_kernel<6>;
+    case 7: return hc_scan_dense_kernel<7>;
+    default: return hc_scan_dense_kernel<8>;
+  }
+}
+
+KernelFn emit_kernel_for_q(int q) {
+  switch (q) {
+    case 1: return hc_emit_kernel<1>;
+    case 2: return hc_emit_kernel<2>;
+    case 3: return hc_emit_kernel<3>;
+    case 4: return hc_emit_kernel<4>;
+    case 5: return hc_emit_kernel<5>;
+    case 6: return hc_emit_kernel<6>;
+    case 7: return hc_emit_kernel<7>;
+    default: return hc_emit_kernel<8>;
   }
 }
 
 std::mutex g_attr_mu;
-std::set<std::pair<int, const void*>> g_attr_done;
+std::map<std::pair<int, const void*>, size_t> g_attr_set;  // dynamic smem opted in
 
+// Raises the kernel's dynamic shared-memory limit to at least `smem` bytes.
 int ensure_smem_attr(int dev, KernelFn fn, size_t smem) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
   auto key = std::make_pair(dev, reinterpret_cast<const void*>(fn));
-  if (g_attr_done.count(key)) return HC_OK;
-  const DeviceInfo& di = device_info(dev);
+  auto it = g_attr_set.find(key);
+  if (it != g_attr_set.end() && it->second >= smem) return HC_OK;
   cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(di.smem_optin));
+                                       static_cast<int>(smem));
   if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
-  g_attr_done.insert(key);
-  (void)smem;
+  g_attr_set[key] = smem;
   return HC_OK;
 }
 
-struct Plan {
-  bool staged;
-  int L;
-  uint32_t C, stage_bytes, x_smem;
-  size_t smem;
-  unsigned long long num_chunks;
-};
+// Static shared memory of a kernel (counts against the per-block limit).
+size_t static_smem(KernelFn fn) {
+  static std::mutex mu;
+  static std::map<const void*, size_t> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(reinterpret_cast<const void*>(fn));
+  if (it != cache.end()) return it->second;
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(fn)) != cudaSuccess) return 1024;
+  cache[reinterpret_cast<const void*>(fn)] = fa.sharedSizeBytes;
+  return fa.sharedSizeBytes;
+}
 
-Plan make_plan(const Filter* f, size_t n, size_t smem_limit, bool staged) {
-  Plan p{};
-  const int m = static_cast<int>(std::min<size_t>(f->m, 1u << 30));
-  const int shift = m - f->q + 1;
-  p.staged = staged;
-  // L = 4 * (odd number of words) >= max(64, 4 * shift), at most 188 bytes
-  int lw = std::max(16, shift) | 1;
-  lw = std::min(lw, 47);
-  p.L = 4 * lw;
-  p.C = static_cast<uint32_t>(kThreads * p.L);
-  p.stage_bytes = static_cast<uint32_t>(((16 + p.C + f->m - 1 + 15) & ~size_t(15)) + 16);
-  p.x_smem = f->m <= static_cast<size_t>(kMaxSmemX) ? static_cast<uint32_t>((f->m + 15) & ~size_t(15)) : 0u;
-  const size_t fbytes = (f->F.size() * 4 + 15) & ~size_t(15);
-  p.smem = fbytes + p.x_smem + (p.staged ? size_t(kStages) * p.stage_bytes : 0) +
-           size_t(kSlots) * kThreads * 4;
-  const unsigned long long nwin = n - f->m + 1;
-  p.num_chunks = (nwin + p.C - 1) / p.C;
-  (void)smem_limit;
-  return p;
+// Resident CTAs per SM of a kernel at a given dynamic shared memory size.
+int occupancy(int dev, KernelFn fn, size_t smem, int* per_sm) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, size_t>, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(dev, reinterpret_cast<const void*>(fn), smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *per_sm = it->second;
+    return HC_OK;
+  }
+  int v = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn, kThreads, smem);
+  if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  cache[key] = v;
+  *per_sm = v;
+  return HC_OK;
 }
 
 }  // namespace
 
-// Enqueues the search; count_dev receives the total.  Internal entry shared
-// by the C ABI functions.
-int launch_search(Filter* f, const uint8_t* y, size_t n, uint64_t* pos, size_t cap,
-                  uint64_t* count_dev, cudaStream_t stream) {
-  int rc = filter_to_device(f);
-  if (rc != HC_OK) return rc;
-  cudaError_t e;
-  if (n < f->m) {
-    e = cudaMemsetAsync(count_dev, 0, sizeof(uint64_t), stream);
-    return e == cudaSuccess ? HC_OK : cuda_error(e, "cudaMemsetAsync(count)");
-  }
-  int dev = 0;
-  e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+// Chooses the launch shape for one search (see SearchPlan in hc_internal.h).
+// Kinds: dense (m = q: every window in turn, warp-cooperative), staged
+// (per-lane HC over text staged in shared memory) and direct (per-lane HC
+// reading the text from global memory: long patterns, whose large shifts
+// skip most of the text, and patterns too long to stage).
+int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, int dev,
+                SearchPlan* out) {
+  SearchPlan p{};
   const DeviceInfo& di = device_info(dev);
-  Plan p = make_plan(f, n, di.smem_optin, f->m <= kMaxStagedM);
-  if (p.staged && p.smem > di.smem_optin) p = make_plan(f, n, di.smem_optin, false);
-  if (p.smem > di.smem_optin)
-    return set_error(HC_ERR_ARG, "hc_search: filter exceeds shared memory");
-  KernelFn fn = p.staged ? kernel_for_q<true>(f->q) : kernel_for_q<false>(f->q);
-  rc = ensure_smem_attr(dev, fn, p.smem);
+  const int m = static_cast<int>(std::min<size_t>(f->m, size_t(1) << 30));
+  const int shift = m - f->q + 1;
+  const int mode = o ? o->mode : HC_MODE_AUTO;
+  if (mode < HC_MODE_AUTO || mode > HC_MODE_DENSE)
+    return set_error(HC_ERR_ARG, "hc_search: unknown mode");
+  if (mode == HC_MODE_DENSE && f->m != static_cast<size_t>(f->q))
+    return set_error(HC_ERR_ARG, "hc_search: the dense mode needs m = q");
+  int kind = mode;
+  const int L_req = o ? o->lane_bytes : 0;
+  if (kind == HC_MODE_AUTO) {
+    if (f->m == static_cast<size_t>(f->q) && L_req <= 256) kind = HC_MODE_DENSE;
+    else if (shift >= kDirectShift || f->m > kMaxStagedM) kind = HC_MODE_DIRECT;
+    else kind = HC_MODE_STAGED;
+  }
+  int L = L_req;
+  if (L == 0) {
+    if (kind == HC_MODE_DENSE) {
+      L = 32;
+    } else if (kind == HC_MODE_DIRECT) {
+      L = std::min(4096, std::max(64, shift));
+    } else {
+      // 4 * (odd number of words) >= max(64, 4 * shift), at most 188 bytes:
+      // lanes that advance in step read 32 different banks
+      const int lw = std::max(16, shift) | 1;
+      L = 4 * std::min(lw, 47);
+    }
+  }
+  if (L < 1 || L > 4096) return set_error(HC_ERR_ARG, "hc_search: lane_bytes out of [1, 4096]");
+  if (kind == HC_MODE_DENSE && L > 256)
+    return set_error(HC_ERR_ARG, "hc_search: the dense mode needs lane_bytes <= 256");
+  const int stages = o && o->stages ? o->stages : (kind == HC_MODE_DENSE ? 4 : 3);
+  if (stages < 2 || stages > kMaxStages) return set_error(HC_ERR_ARG, "hc_search: stages out of [2, 4]");
+  p.kind = kind;
+  p.L = L;
+  p.C = static_cast<uint32_t>(kThreads) * static_cast<uint32_t>(L);
+  p.stages = stages;
+  p.x_smem = f->m <= static_cast<size_t>(kMaxSmemX) ? static_cast<uint32_t>((f->m + 15) & ~size_t(15)) : 0u;
+  const size_t fbytes = (f->F.size() * 4 + 15) & ~size_t(15);
+  const size_t slot_bytes = size_t(kSlots) * kThreads * 4;
+  // staged text: head (< 16) + C + m - 1 bytes, rounded to 16, plus slack for
+  // the word loads that run past the last q-gram
+  p.stage_bytes = static_cast<uint32_t>(((16 + p.C + f->m - 1 + 15) & ~size_t(15)) + 64);
+  if (kind == HC_MODE_DENSE) {
+    p.scan = dense_kernel_for_q(f->q);
+    p.smem_scan = fbytes + size_t(stages) * p.stage_bytes + size_t(p.C) * 2;
+  } else if (kind == HC_MODE_STAGED) {
+    p.scan = scan_kernel_for_q<true>(f->q);
+    p.smem_scan = fbytes + p.x_smem + size_t(stages) * p.stage_bytes + slot_bytes;
+    if (p.smem_scan + static_smem(p.scan) > di.smem_optin) {
+      if (mode == HC_MODE_STAGED)
+        return set_error(HC_ERR_ARG, "hc_search: staging buffers exceed shared memory");
+      p.kind = kind = HC_MODE_DIRECT;
+    }
+  }
+  if (kind == HC_MODE_DIRECT) {
+    p.scan = scan_kernel_for_q<false>(f->q);
+    p.smem_scan = fbytes + p.x_smem + slot_bytes;
+  }
+  if (p.smem_scan + static_smem(p.scan) > di.smem_optin)
+    return set_error(HC_ERR_ARG, "hc_search: filter and buffers exceed shared memory");
+  p.emit = emit_kernel_for_q(f->q);
+  p.smem_emit = (((f->F.size() + 3) & ~size_t(3)) * 4) + slot_bytes;
+
+  int rc = ensure_smem_attr(dev, p.scan, p.smem_scan);
+  if (rc != HC_OK) return rc;
+  rc = ensure_smem_attr(dev, p.emit, p.smem_emit);
   if (rc != HC_OK) return rc;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, p.smem);
-  if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  rc = occupancy(dev, p.scan, p.smem_scan, &per_sm);
+  if (rc != HC_OK) return rc;
   per_sm = std::max(per_sm, 1);
-  const unsigned long long grid =
-      std::min<unsigned long long>(p.num_chunks, static_cast<unsigned long long>(per_sm) * di.sm_count);
+  if (o && o->ctas_per_sm > 0) per_sm = std::min(per_sm, o->ctas_per_sm);
 
-  const size_t ws_bytes = (p.num_chunks + 1) * sizeof(unsigned long long);
-  void* ws = nullptr;
-  e = cudaMallocAsync(&ws, ws_bytes, stream);
-  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(workspace)");
-  e = cudaMemsetAsync(ws, 0, ws_bytes, stream);
-  if (e != cudaSuccess) {
-    cudaFreeAsync(ws, stream);
-    return cuda_error(e, "cudaMemsetAsync(workspace)");
-  }
+  const unsigned long long nwin = n - f->m + 1;
+  p.num_chunks = (nwin + p.C - 1) / p.C;
+  unsigned long long grid = std::min<unsigned long long>(p.num_chunks,
+                                                         static_cast<unsigned long long>(per_sm) * di.sm_count);
+  p.chunks_per_cta = (p.num_chunks + grid - 1) / grid;
+  if (p.chunks_per_cta * p.C >= (1ull << 32))
+    return set_error(HC_ERR_ARG, "hc_search: text too long for one launch");
+  p.grid = (p.num_chunks + p.chunks_per_cta - 1) / p.chunks_per_cta;
+  unsigned long long spill = o ? o->spill_entries : 0;
+  if (spill == 0)
+    spill = cap == 0 ? 0 : std::min<unsigned long long>(nwin, std::max<unsigned long long>(cap, 1ull << 20));
+  p.region_entries = (std::max<unsigned long long>(1, (spill + p.grid - 1) / p.grid) + 3) & ~3ull;
+  p.ws_bytes = p.grid * 16 + p.grid * p.region_entries * 4;
+  *out = p;
+  return HC_OK;
+}
 
-  SearchArgs a{};
+void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n, uint64_t* pos,
+               size_t cap, uint64_t* count_dev, void* ws, void* args_out) {
+  SearchArgs& a = *static_cast<SearchArgs*>(args_out);
+  a = SearchArgs{};
   a.y = y;
   a.n = n;
   a.nwin = n - f->m + 1;
@@ -466,21 +788,67 @@ int launch_search(Filter* f, const uint8_t* y, size_t n, uint64_t* pos, size_t c
   a.pos = reinterpret_cast<unsigned long long*>(pos);
   a.cap = pos ? cap : 0;
   a.count_out = reinterpret_cast<unsigned long long*>(count_dev);
-  a.claim = static_cast<unsigned long long*>(ws);
-  a.state = static_cast<unsigned long long*>(ws) + 1;
+  a.cta_total = static_cast<unsigned long long*>(ws);
+  a.cta_overflow = a.cta_total + p.grid;
+  a.region = reinterpret_cast<uint32_t*>(a.cta_overflow + p.grid);
+  a.region_entries = p.region_entries;
   a.num_chunks = p.num_chunks;
+  a.chunks_per_cta = p.chunks_per_cta;
   a.L = p.L;
   a.C = p.C;
   a.head = static_cast<int>(reinterpret_cast<uintptr_t>(y) & 15u);
   a.stage_bytes = p.stage_bytes;
   a.x_smem = p.x_smem;
+  a.stages = p.stages;
+  // byte groups of h: the longest prefix whose weights 2^(s*k) fit in a byte
+  const int s = f->s, q = f->q;
+  int g = 1;
+  while (g < 4 && g < q && s * g <= 7) ++g;
+  a.g0 = g;
+  a.w0 = 0;
+  for (int k = 0; k < g; ++k) a.w0 |= (1u << (s * k)) << (8 * k);
+  a.w1 = 0;
+  for (int k = 0; k < q - g && k < 4; ++k) a.w1 |= (1u << (s * k)) << (8 * k);
+}
 
-  fn<<<static_cast<unsigned>(grid), kThreads, p.smem, stream>>>(a);
+// Enqueues the two kernels of one search with a caller-supplied workspace.
+int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n, uint64_t* pos,
+                   size_t cap, uint64_t* count_dev, void* ws, cudaStream_t stream) {
+  SearchArgs a;
+  fill_args(f, p, y, n, pos, cap, count_dev, ws, &a);
+  p.scan<<<static_cast<unsigned>(p.grid), kThreads, p.smem_scan, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
+  p.emit<<<static_cast<unsigned>(p.grid), kThreads, p.smem_emit, stream>>>(a);
   e = cudaGetLastError();
-  g_launches.fetch_add(1);
-  cudaFreeAsync(ws, stream);
-  if (e != cudaSuccess) return cuda_error(e, "hc_search kernel launch");
+  g_launches.fetch_add(2);
+  if (e != cudaSuccess) return cuda_error(e, "hc_emit_kernel launch");
   return HC_OK;
+}
+
+// Enqueues one search; the workspace comes from the library's stream-ordered
+// pool and goes back to it after the kernels.
+int launch_search(Filter* f, const uint8_t* y, size_t n, uint64_t* pos, size_t cap,
+                  uint64_t* count_dev, const hc_search_opts* o, cudaStream_t stream) {
+  int rc = filter_to_device(f);
+  if (rc != HC_OK) return rc;
+  cudaError_t e;
+  if (n < f->m) {
+    e = cudaMemsetAsync(count_dev, 0, sizeof(uint64_t), stream);
+    return e == cudaSuccess ? HC_OK : cuda_error(e, "cudaMemsetAsync(count)");
+  }
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  SearchPlan p;
+  rc = plan_search(f, n, pos ? cap : 0, o, dev, &p);
+  if (rc != HC_OK) return rc;
+  void* ws = nullptr;
+  e = cudaMallocFromPoolAsync(&ws, p.ws_bytes, device_pool(dev), stream);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocFromPoolAsync(workspace)");
+  rc = launch_planned(f, p, y, n, pos, cap, count_dev, ws, stream);
+  cudaFreeAsync(ws, stream);
+  return rc;
 }
 
 int read_and_clear_status(cudaStream_t stream) {
@@ -501,35 +869,61 @@ int read_and_clear_status(cudaStream_t stream) {
 
 using namespace hc;
 
+namespace {
+int check_search_args(const char* who, Filter* f, const uint8_t* y_dev, size_t n,
+                      const uint64_t* pos_dev, size_t cap) {
+  if (f == nullptr) return set_error(HC_ERR_ARG, std::string(who) + ": invalid filter");
+  if (y_dev == nullptr && n > 0) return set_error(HC_ERR_ARG, std::string(who) + ": y_dev is NULL");
+  if (pos_dev == nullptr && cap > 0)
+    return set_error(HC_ERR_ARG, std::string(who) + ": pos_dev is NULL with cap > 0");
+  return HC_OK;
+}
+}  // namespace
+
 extern "C" {
+
+int hc_search_ex(const hc_filter* fp, const uint8_t* y_dev, size_t n, uint64_t* pos_dev,
+                 size_t cap, uint64_t* count_dev, const hc_search_opts* opts,
+                 hc_stream_t stream) {
+  clear_error();
+  Filter* f = as_filter(fp);
+  int rc = check_search_args("hc_search_ex", f, y_dev, n, pos_dev, cap);
+  if (rc != HC_OK) return rc;
+  if (count_dev == nullptr) return set_error(HC_ERR_ARG, "hc_search_ex: count_dev is NULL");
+  if (opts != nullptr && opts->struct_size != sizeof(hc_search_opts))
+    return set_error(HC_ERR_ARG, "hc_search_ex: opts->struct_size mismatch");
+  return launch_search(f, y_dev, n, pos_dev, cap, count_dev, opts,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
 
 int hc_search_async(const hc_filter* fp, const uint8_t* y_dev, size_t n, uint64_t* pos_dev,
                     size_t cap, uint64_t* count_dev, hc_stream_t stream) {
   clear_error();
   Filter* f = as_filter(fp);
-  if (f == nullptr) return set_error(HC_ERR_ARG, "hc_search_async: invalid filter");
+  int rc = check_search_args("hc_search_async", f, y_dev, n, pos_dev, cap);
+  if (rc != HC_OK) return rc;
   if (count_dev == nullptr) return set_error(HC_ERR_ARG, "hc_search_async: count_dev is NULL");
-  if (y_dev == nullptr && n > 0) return set_error(HC_ERR_ARG, "hc_search_async: y_dev is NULL");
-  if (pos_dev == nullptr && cap > 0)
-    return set_error(HC_ERR_ARG, "hc_search_async: pos_dev is NULL with cap > 0");
-  return launch_search(f, y_dev, n, pos_dev, cap, count_dev, reinterpret_cast<cudaStream_t>(stream));
+  return launch_search(f, y_dev, n, pos_dev, cap, count_dev, nullptr,
+                       reinterpret_cast<cudaStream_t>(stream));
 }
 
 int hc_search(const hc_filter* fp, const uint8_t* x, const uint8_t* y_dev, size_t n,
               uint64_t* pos_dev, size_t cap, size_t* count, hc_stream_t stream_) {
   clear_error();
   Filter* f = as_filter(fp);
-  if (f == nullptr) return set_error(HC_ERR_ARG, "hc_search: invalid filter");
+  int rc = check_search_args("hc_search", f, y_dev, n, pos_dev, cap);
+  if (rc != HC_OK) return rc;
   if (x == nullptr || count == nullptr) return set_error(HC_ERR_ARG, "hc_search: x or count is NULL");
   if (std::memcmp(x, f->x.data(), f->m) != 0)
     return set_error(HC_ERR_ARG, "hc_search: x is not the pattern the filter was built from");
-  if (y_dev == nullptr && n > 0) return set_error(HC_ERR_ARG, "hc_search: y_dev is NULL");
-  if (pos_dev == nullptr && cap > 0) return set_error(HC_ERR_ARG, "hc_search: pos_dev is NULL with cap > 0");
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
   void* cnt_dev = nullptr;
-  cudaError_t e = cudaMallocAsync(&cnt_dev, sizeof(uint64_t), stream);
-  if (e != cudaSuccess) return cuda_error(e, "cudaMallocAsync(count)");
-  int rc = launch_search(f, y_dev, n, pos_dev, cap, static_cast<uint64_t*>(cnt_dev), stream);
+  e = cudaMallocFromPoolAsync(&cnt_dev, sizeof(uint64_t), device_pool(dev), stream);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocFromPoolAsync(count)");
+  rc = launch_search(f, y_dev, n, pos_dev, cap, static_cast<uint64_t*>(cnt_dev), nullptr, stream);
   unsigned long long host_count = 0;
   if (rc == HC_OK) {
     e = cudaMemcpyAsync(&host_count, cnt_dev, sizeof host_count, cudaMemcpyDeviceToHost, stream);

@@ -107,6 +107,21 @@ def test_degenerate_inputs():
                     assert np.array_equal(got, want), (bytes(x[:8]), y.size, q, alpha, off)
 
 
+def test_every_q_alpha_pair():
+    """All 8 x 15 (q, alpha) pairs: s = floor(alpha/q) covers every byte
+    grouping of the hash, including s = 0 and s >= 8."""
+    rng = np.random.default_rng(88)
+    for sigma in (4, 95):
+        x, y = _case(rng, sigma, 60_000, 9, plant=20)
+        for q in range(1, 9):
+            for alpha in range(1, 16):
+                got = gpu_positions(x, y, q, alpha)
+                assert np.array_equal(got, oracle.hc_search(x, y, q, alpha)), (sigma, q, alpha)
+        xq = x[:4]
+        for alpha in range(1, 16):          # m = q = 4: the dense kernel
+            assert np.array_equal(gpu_positions(xq, y, 4, alpha), oracle.naive_search(xq, y))
+
+
 def test_alpha_below_q_and_large_alpha():
     rng = np.random.default_rng(77)
     x, y = _case(rng, 4, 500_000, 24, plant=30)
@@ -134,7 +149,7 @@ def test_capacity_error_writes_prefix():
         hc.hc_search(f, x, y_dev, pos, 100)
     assert ei.value.code == hc.HC_ERR_CAPACITY
     assert pos.cpu().numpy().tolist() == list(range(100))
-    assert hc.hc_search(f, x, y_dev, None, 0) == 9_999
+    assert hc.hc_search(f, x, y_dev, None, 0, allow_truncated=True) == 9_999
     with pytest.raises(hc.HCError) as ei:
         hc.hc_search(f, b"AB", y_dev, None, 0)     # not the filter's pattern
     assert ei.value.code == hc.HC_ERR_ARG
@@ -157,6 +172,73 @@ def test_async_entry_point_and_count():
     assert int(cnt.item()) == want.size
     assert np.array_equal(pos[:want.size].cpu().numpy().view(np.uint64), want)
     assert int(pos[want.size].item()) == -1     # nothing written past the count
+
+
+@pytest.mark.parametrize("opts", [
+    dict(spill_entries=1), dict(spill_entries=100), dict(lane_bytes=4, stages=2),
+    dict(lane_bytes=37, stages=4), dict(lane_bytes=1000, stages=2, ctas_per_sm=1),
+    dict(lane_bytes=260, spill_entries=5000), dict(mode=1, lane_bytes=68),
+    dict(mode=2), dict(mode=2, lane_bytes=3001, spill_entries=77), dict(mode=2, lane_bytes=8)])
+def test_launch_options_and_spill_overflow(opts):
+    """Every launch shape gives the same positions, including spill regions
+    too small for the occurrences (the emit kernel re-scans those chunks)."""
+    hc = _hc()
+    rng = np.random.default_rng(31)
+    for sigma, m, n in [(2, 3, 700_001), (4, 8, 1_500_000), (20, 2, 333_333), (1, 5, 100_000)]:
+        x, y = _case(rng, sigma, n, m, plant=50)
+        q, alpha = min(m, 3), 11
+        want = oracle.hc_search(x, y, q, alpha)
+        y_dev, keep = _upload(y, offset=int(rng.integers(0, 16)))
+        f = hc.hc_preprocess(x, q, alpha)
+        for cap in (want.size + 3, max(want.size // 3, 1)):
+            pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(**opts))
+            torch.cuda.synchronize()
+            hc.hc_check_status()
+            assert int(cnt.item()) == want.size, (sigma, m, opts)
+            k = min(cap, want.size)
+            got = pos[:k].cpu().numpy().view(np.uint64)
+            assert np.array_equal(got, want[:k]), (sigma, m, opts, cap)
+        f.free()
+
+
+@pytest.mark.parametrize("opts", [
+    dict(mode=3), dict(mode=3, lane_bytes=1), dict(mode=3, lane_bytes=128, stages=2),
+    dict(mode=3, lane_bytes=33, spill_entries=10), dict(mode=3, spill_entries=1),
+    dict(mode=3, lane_bytes=5, ctas_per_sm=1, stages=3)])
+def test_dense_mode_m_equals_q(opts):
+    """m = q: the warp-cooperative kernel against the oracle, for every q."""
+    hc = _hc()
+    rng = np.random.default_rng(41)
+    for sigma, m, n in [(2, 2, 1_000_003), (4, 4, 600_000), (20, 3, 250_001), (1, 5, 70_000),
+                        (95, 8, 400_000), (2, 1, 100_000), (3, 6, 500_000), (4, 7, 123_457)]:
+        x, y = _case(rng, sigma, n, m, plant=40)
+        want = oracle.hc_search(x, y, m, 12)
+        y_dev, keep = _upload(y, offset=int(rng.integers(0, 16)))
+        f = hc.hc_preprocess(x, m, 12)
+        for cap in (want.size + 1, max(want.size // 2, 1)):
+            pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(**opts))
+            torch.cuda.synchronize()
+            hc.hc_check_status()
+            assert int(cnt.item()) == want.size, (sigma, m, opts)
+            k = min(cap, want.size)
+            assert np.array_equal(pos[:k].cpu().numpy().view(np.uint64), want[:k]), (sigma, m, opts)
+        f.free()
+
+
+def test_search_opts_rejected_when_out_of_range():
+    hc = _hc()
+    y_dev, keep = _upload(np.frombuffer(b"ACGT" * 1000, np.uint8))
+    f = hc.hc_preprocess(b"ACGTACGT", 4, 12)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for bad in (dict(lane_bytes=5000), dict(stages=5), dict(stages=1), dict(mode=3),
+                dict(mode=7)):
+        with pytest.raises(hc.HCError) as ei:
+            hc.hc_search_ex(f, y_dev, None, cnt, hc.SearchOpts(**bad))
+        assert ei.value.code == hc.HC_ERR_ARG
 
 
 def test_full_size_sweep_texts():
