@@ -162,6 +162,37 @@ int hc_search(const hc_filter *f, const uint8_t *x, const uint8_t *y_dev,
               size_t n, uint64_t *pos_dev, size_t cap, size_t *count,
               hc_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * hc_search_noalloc: the search of hc_search_async for callers that cannot
+ * allocate device memory -- e.g. code running while a CUDA graph is captured
+ * on its stream, applications whose device memory is planned in full by
+ * their own allocator or arena, or latency-critical paths that must not
+ * enter an allocator.  The paper has no counterpart: this is an interface of
+ * this library only.
+ *
+ * It allocates nothing (no cudaMalloc, cudaFree or pool allocation): the
+ * caller passes every buffer -- F_dev, the filter's 2^alpha words as returned
+ * by hc_filter_words, and x_dev, its m pattern bytes, both copied by the
+ * caller into device memory; the text y_dev; the output pos_dev (cap
+ * positions, may be NULL when cap = 0) and count_dev (one uint64).  The
+ * scratch that holds occurrences until their output offsets are known is a
+ * fixed 8 MiB array inside the library, held by every GPU that loads the
+ * library until the process exits.  Limit: min(cap, n-m+1) at most 2,000,000
+ * positions; larger requests are rejected with HC_ERR_ARG (the count alone,
+ * cap = 0, works for any n).  Results and the other errors are those of
+ * hc_search_async; nothing is waited for.
+ *
+ * The first call on each device looks up the scratch's device address and
+ * prepares the kernels; make that first call before capturing a stream.  All
+ * calls on a device share the one scratch array and it keeps the last
+ * call's contents: calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.
+ */
+int hc_search_noalloc(const hc_filter *f, const uint32_t *F_dev,
+                      const uint8_t *x_dev, const uint8_t *y_dev, size_t n,
+                      uint64_t *pos_dev, size_t cap, uint64_t *count_dev,
+                      hc_stream_t stream);
+
 /* Waits for `stream` and reports (and clears) any device-side error flag
  * raised by the library's kernels on the current device: HC_ERR_TIMEOUT if a
  * bounded wait gave up, else HC_OK.  Errors: HC_ERR_CUDA. */

@@ -63,6 +63,7 @@ SIGNATURES = {
     "hc_search_async": (ctypes.c_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp]),
     "hc_search": (ctypes.c_int, [_vp, _vp, _vp, _sz, _vp, _sz, ctypes.POINTER(_sz), _vp]),
     "hc_search_ex": (ctypes.c_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _vp]),
+    "hc_search_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, _sz, _vp, _vp]),
     "hc_check_status": (ctypes.c_int, [_vp]),
     "hc_kernel_launches": (ctypes.c_uint64, []),
 }
@@ -249,6 +250,21 @@ def search_positions(f: HCFilter, x, y_dev, stream=None):
     count2 = hc_search(f, x, y_dev, pos, count, stream)
     assert count2 == count
     return pos[:count]
+
+
+def hc_search_noalloc(f: HCFilter, F_dev, x_dev, y_dev, pos_dev, count_dev,
+                      cap: int | None = None, n: int | None = None, stream=None) -> None:
+    """hc_search_noalloc: the search with every buffer supplied by the caller
+    (F_dev: the filter's words, x_dev: the pattern, both on the device); the
+    library allocates nothing."""
+    n = y_dev.numel() if n is None else int(n)
+    if pos_dev is None:
+        cap = 0
+    elif cap is None:
+        cap = pos_dev.numel()
+    _check(lib().hc_search_noalloc(f.handle, _dev_ptr(F_dev), _dev_ptr(x_dev), _dev_ptr(y_dev), n,
+                                   _dev_ptr(pos_dev), int(cap), _dev_ptr(count_dev),
+                                   _stream_handle(stream)), "hc_search_noalloc")
 
 
 def hc_check_status(stream=None) -> None:

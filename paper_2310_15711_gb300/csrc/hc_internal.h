@@ -83,5 +83,8 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
 int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
                    uint64_t* pos, size_t cap, uint64_t* count_dev, void* ws,
                    cudaStream_t stream);
+int launch_planned_filter_ptrs(const Filter* f, const SearchPlan& p, const uint32_t* F_dev,
+                               const uint8_t* x_dev, const uint8_t* y, size_t n, uint64_t* pos,
+                               size_t cap, uint64_t* count_dev, void* ws, cudaStream_t stream);
 
 }  // namespace hc

@@ -826,6 +826,25 @@ int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_
   return HC_OK;
 }
 
+// Enqueues the two kernels of one search reading the filter words and the
+// pattern from caller-supplied device copies instead of the filter's own.
+int launch_planned_filter_ptrs(const Filter* f, const SearchPlan& p, const uint32_t* F_dev,
+                               const uint8_t* x_dev, const uint8_t* y, size_t n, uint64_t* pos,
+                               size_t cap, uint64_t* count_dev, void* ws, cudaStream_t stream) {
+  SearchArgs a;
+  fill_args(f, p, y, n, pos, cap, count_dev, ws, &a);
+  a.F = F_dev;
+  a.x = x_dev;
+  p.scan<<<static_cast<unsigned>(p.grid), kThreads, p.smem_scan, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
+  p.emit<<<static_cast<unsigned>(p.grid), kThreads, p.smem_emit, stream>>>(a);
+  e = cudaGetLastError();
+  g_launches.fetch_add(2);
+  if (e != cudaSuccess) return cuda_error(e, "hc_emit_kernel launch");
+  return HC_OK;
+}
+
 // Enqueues one search; the workspace comes from the library's stream-ordered
 // pool and goes back to it after the kernels.
 int launch_search(Filter* f, const uint8_t* y, size_t n, uint64_t* pos, size_t cap,
