@@ -134,6 +134,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def scan_family(m: int, q: int) -> str:
+    """The scan kernel the library picks for a pattern (its automatic mode)."""
+    if m == q:
+        return "scan_dense"
+    if m - q + 1 >= 200:
+        return "scan_direct"
+    return "scan_staged"
+
+
+def recorded_traffic(family: str):
+    """DRAM bytes per launch of a kernel family from the committed ncu summary
+    (profiles/traffic.json), if it was taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2310_15711_gb300", "csrc", "hc_search.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = rec.get(family)
+    if not ent or ent.get("source_sha") != sha:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -235,18 +261,14 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     keys = list(cells.keys())
 
-    def one_step(record_launch_events=None, cell_events=None):
+    def one_step(cell_events=None):
         for ci, key in enumerate(keys):
             pats, filters, q, alpha = cells[key]
             y = texts[key[0]]
             if cell_events is not None:
                 cell_events[ci][0].record(stream)
             for pi, f in enumerate(filters):
-                if record_launch_events is not None:
-                    record_launch_events[ci][pi][0].record(stream)
                 hc.hc_search_async(f, y, pos, counts[ci, pi:pi + 1], cap=cap, stream=stream)
-                if record_launch_events is not None:
-                    record_launch_events[ci][pi][1].record(stream)
             if cell_events is not None:
                 cell_events[ci][1].record(stream)
 
@@ -265,13 +287,12 @@ def run_gpu(args, rank, world, local_rank):
         raise RuntimeError("position buffer too small for this workload")
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    launch_ev = [[[ev(), ev()] for _ in range(args.patterns)] for _ in range(ncell)]
-    cell_ev = [[ev(), ev()] for _ in range(ncell)]
+    cell_ev = [[[ev(), ev()] for _ in range(ncell)] for _ in range(args.steps)]
     step_ev = [[ev(), ev()] for _ in range(args.steps)]
-    launch_ms = np.zeros((ncell, args.patterns))
-    cell_ms = np.zeros(ncell)
 
     sampler = ClockSampler(local_rank)
+    hc.hc_timing_report(reset=True)
+    hc.hc_timing_enable(True)
     launches0 = hc.hc_kernel_launches()
     barrier()
     sampler.start()
@@ -279,20 +300,18 @@ def run_gpu(args, rank, world, local_rank):
     for k in range(args.steps):
         step_ev[k][0].record(stream)
         with torch.cuda.stream(stream):
-            one_step(launch_ev, cell_ev)
+            one_step(cell_ev[k])
         step_ev[k][1].record(stream)
-        # per-launch and per-cell times of this step (read after the sync below)
-        stream.synchronize()
-        for ci in range(ncell):
-            cell_ms[ci] += cell_ev[ci][0].elapsed_time(cell_ev[ci][1])
-            for pi in range(args.patterns):
-                launch_ms[ci, pi] += launch_ev[ci][pi][0].elapsed_time(launch_ev[ci][pi][1])
     barrier()
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     launches = hc.hc_kernel_launches() - launches0
+    hc.hc_timing_enable(False)
+    kernel_times = hc.hc_timing_report(reset=True)   # {family: (ms, launches)}
     hc.hc_check_status(stream)
     step_ms = float(sum(e[0].elapsed_time(e[1]) for e in step_ev))
+    cell_ms = np.array([sum(cell_ev[k][ci][0].elapsed_time(cell_ev[k][ci][1])
+                            for k in range(args.steps)) for ci in range(ncell)])
 
     t_local = torch.tensor([step_ms], dtype=torch.float64, device=dev)
     if dist is not None:
@@ -303,26 +322,29 @@ def run_gpu(args, rank, world, local_rank):
     value = world * text_bytes_step * args.steps / (step_ms_max / 1e3) / GB
     ms_per_step = step_ms_max / args.steps
 
-    # roofline of the search kernel: algorithmic bytes = text read + 8 bytes
-    # per position written + pattern and filter, per launch
+    # algorithmic bytes per kernel family (per step): the scan kernels read
+    # the text once and spill 4 bytes per occurrence; the emit kernel reads
+    # those 4 and writes the 8-byte position
     cnt = counts.cpu().numpy()
-    algo_bytes = 0.0
+    fam_bytes = {}
     per_cell = {}
     for ci, (s, m) in enumerate(keys):
         pats, filters, q, alpha = cells[(s, m)]
         n = texts[s].numel()
-        cb = float(n * args.patterns + 8 * cnt[ci].sum() + args.patterns * (m + 4 * (1 << alpha)))
-        algo_bytes += cb
+        occ = float(cnt[ci].sum())
+        fam = scan_family(m, q)
+        fam_bytes[fam] = fam_bytes.get(fam, 0.0) + n * args.patterns + 4 * occ
+        fam_bytes["emit"] = fam_bytes.get("emit", 0.0) + 12 * occ
         per_cell[f"s{s}_m{m}"] = {
             "GBps": round(n * args.patterns * args.steps / (cell_ms[ci] / 1e3) / GB, 1),
-            "hbm_frac": None,
+            "kernel": fam, "q": q, "alpha": alpha,
             "occ_per_pattern": float(cnt[ci].mean()),
         }
-        per_cell[f"s{s}_m{m}"]["hbm_frac"] = round(
-            cb * args.steps / (launch_ms[ci].sum() / 1e3) / GB / measured_peaks()[0], 3)
-    kernel_ms_total = float(launch_ms.sum())
-    achieved = algo_bytes * args.steps / (kernel_ms_total / 1e3) / GB
+    dominant = max(kernel_times, key=lambda k: kernel_times[k][0])
+    dom_ms, dom_launches = kernel_times[dominant]
+    achieved = fam_bytes.get(dominant, 0.0) * args.steps / (dom_ms / 1e3) / GB if dom_ms else 0.0
     peak, peak_kind = measured_peaks()
+    traffic = recorded_traffic(dominant)
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
@@ -330,10 +352,11 @@ def run_gpu(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic", "config": workload_config(args),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "hc_search_kernel (+ its workspace memset, same event pair)",
-                     "launches_per_step": ncell * args.patterns},
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": f"hc_{dominant}", "launches": dom_launches,
+                     "avg_launch_us": round(dom_ms * 1e3 / max(dom_launches, 1), 2),
+                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+        "kernel_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kernel_times.items() if v[1]},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "cells": per_cell,

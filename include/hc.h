@@ -202,6 +202,19 @@ int hc_check_status(hc_stream_t stream);
  * process (all devices, all entry points). */
 uint64_t hc_kernel_launches(void);
 
+/* Kernel timing, a profiling aid.  hc_timing_enable(1) makes every later
+ * kernel launch of the library record a CUDA event pair around itself on its
+ * stream (0 stops it).  hc_timing_report waits for the recorded launches and
+ * writes, for kernel families 0..nkinds-1, the summed elapsed milliseconds
+ * (ms[k]) and launch counts (launches[k]); either array may be NULL.  With
+ * reset != 0 the recorded launches are then forgotten.  Families:
+ * hc_timing_kind_name(k) for k = 0.. ("scan_staged", "scan_direct",
+ * "scan_dense", "emit", "preprocess", "batch"; "" past the last).  Errors:
+ * HC_ERR_CUDA. */
+int hc_timing_enable(int on);
+int hc_timing_report(double *ms, uint64_t *launches, int nkinds, int reset);
+const char *hc_timing_kind_name(int kind);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,10 @@ SIGNATURES = {
     "hc_search_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, _sz, _vp, _vp]),
     "hc_check_status": (ctypes.c_int, [_vp]),
     "hc_kernel_launches": (ctypes.c_uint64, []),
+    "hc_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+    "hc_timing_report": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.c_int]),
+    "hc_timing_kind_name": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
 
@@ -273,6 +277,24 @@ def hc_check_status(stream=None) -> None:
 
 def hc_kernel_launches() -> int:
     return int(lib().hc_kernel_launches())
+
+
+def hc_timing_enable(on: bool = True) -> None:
+    _check(lib().hc_timing_enable(1 if on else 0), "hc_timing_enable")
+
+
+def hc_timing_report(reset: bool = True) -> dict:
+    """{kernel family: (milliseconds, launches)} of the timed launches."""
+    k = 16
+    ms = (ctypes.c_double * k)()
+    cnt = (ctypes.c_uint64 * k)()
+    _check(lib().hc_timing_report(ms, cnt, k, 1 if reset else 0), "hc_timing_report")
+    out = {}
+    for i in range(k):
+        name = lib().hc_timing_kind_name(i).decode()
+        if name:
+            out[name] = (float(ms[i]), int(cnt[i]))
+    return out
 
 
 def hc_version() -> int:

@@ -29,6 +29,65 @@ std::unordered_map<int, DeviceInfo> g_dev_info;
 
 std::atomic<uint64_t> g_launches{0};
 
+const char* const kKindNames[kNumKinds] = {"scan_staged", "scan_direct", "scan_dense",
+                                           "emit", "preprocess", "batch"};
+
+namespace {
+std::atomic<bool> g_timing_on{false};
+std::mutex g_timing_mu;
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t ev0, ev1;
+};
+std::vector<TimedLaunch> g_timed;       // recorded, not yet summed
+std::vector<cudaEvent_t> g_event_pool;  // free events
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+bool timing_enabled() { return g_timing_on.load(std::memory_order_relaxed); }
+
+TimingToken timing_begin(int kind, cudaStream_t stream) {
+  TimingToken t;
+  if (!timing_enabled()) return t;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  t.ev0 = take_event();
+  if (t.ev0 == nullptr) return t;
+  if (cudaEventRecord(t.ev0, stream) != cudaSuccess) {
+    cudaGetLastError();
+    g_event_pool.push_back(t.ev0);
+    t.ev0 = nullptr;
+    return t;
+  }
+  t.kind = kind;
+  return t;
+}
+
+void timing_end(const TimingToken& t, cudaStream_t stream) {
+  if (t.ev0 == nullptr) return;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  cudaEvent_t ev1 = take_event();
+  if (ev1 == nullptr || cudaEventRecord(ev1, stream) != cudaSuccess) {
+    cudaGetLastError();
+    g_event_pool.push_back(t.ev0);
+    if (ev1) g_event_pool.push_back(ev1);
+    return;
+  }
+  g_timed.push_back({t.kind, t.ev0, ev1});
+}
+
 int set_error(int code, const std::string& msg) {
   t_last_error = msg;
   return code;
@@ -114,6 +173,43 @@ int hc_version(void) { return 100; }
 const char* hc_last_error(void) { return t_last_error.c_str(); }
 
 uint64_t hc_kernel_launches(void) { return g_launches.load(); }
+
+int hc_timing_enable(int on) {
+  g_timing_on.store(on != 0);
+  return HC_OK;
+}
+
+int hc_timing_report(double* ms, uint64_t* launches, int nkinds, int reset) {
+  clear_error();
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  std::vector<double> acc(kNumKinds, 0.0);
+  std::vector<uint64_t> cnt(kNumKinds, 0);
+  for (const TimedLaunch& t : g_timed) {
+    cudaError_t e = cudaEventSynchronize(t.ev1);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventSynchronize(timing)");
+    float v = 0.f;
+    e = cudaEventElapsedTime(&v, t.ev0, t.ev1);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventElapsedTime(timing)");
+    acc[t.kind] += v;
+    cnt[t.kind] += 1;
+  }
+  for (int k = 0; k < nkinds && k < kNumKinds; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  if (reset) {
+    for (const TimedLaunch& t : g_timed) {
+      g_event_pool.push_back(t.ev0);
+      g_event_pool.push_back(t.ev1);
+    }
+    g_timed.clear();
+  }
+  return HC_OK;
+}
+
+const char* hc_timing_kind_name(int kind) {
+  return (kind >= 0 && kind < kNumKinds) ? kKindNames[kind] : "";
+}
 
 int hc_preprocess(const uint8_t* x, size_t m, int q, int alpha, hc_filter** out) {
   clear_error();

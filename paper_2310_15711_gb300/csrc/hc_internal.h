@@ -49,6 +49,28 @@ void clear_error();
 // Counts launches of this library's kernels.
 extern std::atomic<uint64_t> g_launches;
 
+// Kernel families for hc_timing_report.
+enum KernelKind {
+  kKindScanStaged = 0,
+  kKindScanDirect = 1,
+  kKindScanDense = 2,
+  kKindEmit = 3,
+  kKindPreprocess = 4,
+  kKindBatch = 5,
+  kNumKinds = 6
+};
+extern const char* const kKindNames[kNumKinds];
+
+// Kernel timing (profiling aid).  When enabled, timing_begin/timing_end
+// record a CUDA event pair around a launch; hc_timing_report sums them.
+bool timing_enabled();
+struct TimingToken {
+  cudaEvent_t ev0 = nullptr;
+  int kind = -1;
+};
+TimingToken timing_begin(int kind, cudaStream_t stream);
+void timing_end(const TimingToken& t, cudaStream_t stream);
+
 // Copies the filter to the current device (once).  Returns an HC_* code.
 int filter_to_device(Filter* f);
 

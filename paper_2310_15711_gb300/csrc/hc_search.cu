@@ -816,11 +816,17 @@ int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_
                    size_t cap, uint64_t* count_dev, void* ws, cudaStream_t stream) {
   SearchArgs a;
   fill_args(f, p, y, n, pos, cap, count_dev, ws, &a);
+  const int kind = p.kind == HC_MODE_DENSE ? kKindScanDense
+                   : (p.kind == HC_MODE_DIRECT ? kKindScanDirect : kKindScanStaged);
+  TimingToken t0 = timing_begin(kind, stream);
   p.scan<<<static_cast<unsigned>(p.grid), kThreads, p.smem_scan, stream>>>(a);
   cudaError_t e = cudaGetLastError();
+  timing_end(t0, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
+  TimingToken t1 = timing_begin(kKindEmit, stream);
   p.emit<<<static_cast<unsigned>(p.grid), kThreads, p.smem_emit, stream>>>(a);
   e = cudaGetLastError();
+  timing_end(t1, stream);
   g_launches.fetch_add(2);
   if (e != cudaSuccess) return cuda_error(e, "hc_emit_kernel launch");
   return HC_OK;
@@ -835,11 +841,17 @@ int launch_planned_filter_ptrs(const Filter* f, const SearchPlan& p, const uint3
   fill_args(f, p, y, n, pos, cap, count_dev, ws, &a);
   a.F = F_dev;
   a.x = x_dev;
+  const int kind = p.kind == HC_MODE_DENSE ? kKindScanDense
+                   : (p.kind == HC_MODE_DIRECT ? kKindScanDirect : kKindScanStaged);
+  TimingToken t0 = timing_begin(kind, stream);
   p.scan<<<static_cast<unsigned>(p.grid), kThreads, p.smem_scan, stream>>>(a);
   cudaError_t e = cudaGetLastError();
+  timing_end(t0, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
+  TimingToken t1 = timing_begin(kKindEmit, stream);
   p.emit<<<static_cast<unsigned>(p.grid), kThreads, p.smem_emit, stream>>>(a);
   e = cudaGetLastError();
+  timing_end(t1, stream);
   g_launches.fetch_add(2);
   if (e != cudaSuccess) return cuda_error(e, "hc_emit_kernel launch");
   return HC_OK;
