@@ -50,7 +50,9 @@ constexpr int kSlots = 4;
 constexpr int kMaxSmemX = 4096;             // larger patterns verify from global memory
 constexpr size_t kMaxStagedM = 16384;       // larger patterns use the unstaged kernel
 constexpr unsigned long long kNoOverflow = ~0ull;
-constexpr int kDirectShift = 200;           // shifts this long skip most 32-byte sectors
+constexpr int kDirectShift = 200;
+constexpr int kEmitSplit = 4;               // CTAs of the emit kernel per record group
+constexpr int kMaxEmitGroup = 64;           // records per emit record group, at most           // shifts this long skip most 32-byte sectors
 
 // bit 0: a bounded device-side wait gave up
 __device__ unsigned int g_status;
@@ -81,6 +83,8 @@ struct SearchArgs {
   uint32_t stage_bytes;      // bytes per staging buffer (16-byte multiple)
   uint32_t x_smem;           // bytes of shared memory for x (0: verify from global)
   int stages;                // staging buffers per CTA (2..kMaxStages)
+  unsigned long long records;     // spill records (per CTA, or per warp when dense)
+  unsigned long long emit_group;  // records served by one emit CTA group
   // h as at most two byte-dot-products (see qgram_hash): bytes [0, g0) with
   // weights w0, bytes [g0, q) with weights w1, scaled by 2^(s*g0)
   uint32_t w0, w1;
@@ -124,14 +128,20 @@ __device__ __forceinline__ void load_qgram(const uint8_t* base, int o, uint32_t*
     *hi = 0;
     if constexpr (Q > 4) *hi = __funnelshift_r(w1, W[wi + 2], r);
   } else {
-    uint32_t l = 0, h = 0;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      const uint32_t b = __ldg(base + o + k);
-      if (k < 4) l |= b << (8 * k); else h |= b << (8 * (k - 4));
-    }
-    *lo = l;
-    *hi = h;
+    // the aligned 8-byte words that overlap the q-gram (one or two); an
+    // aligned word holding a text byte never crosses a page
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(base + o);
+    const unsigned long long* p8 = reinterpret_cast<const unsigned long long*>(addr & ~uintptr_t(7));
+    const uint32_t off = static_cast<uint32_t>(addr & 7u);
+    const unsigned long long d0 = __ldg(p8);
+    const unsigned long long d1 = (off + Q > 8u) ? __ldg(p8 + 1) : 0ull;
+    const uint32_t x0 = static_cast<uint32_t>(d0), x1 = static_cast<uint32_t>(d0 >> 32);
+    const uint32_t x2 = static_cast<uint32_t>(d1), x3 = static_cast<uint32_t>(d1 >> 32);
+    const uint32_t r = (off & 3u) * 8u;
+    const bool up = off >= 4u;  // first byte in the second 32-bit word
+    const uint32_t a0 = up ? x1 : x0, a1 = up ? x2 : x1, a2 = up ? x3 : x2;
+    *lo = __funnelshift_r(a0, a1, r);
+    *hi = Q > 4 ? __funnelshift_r(a1, a2, r) : 0u;
   }
 }
 
@@ -158,60 +168,153 @@ struct Sink {
   unsigned long long obase, vbase, limit;
 };
 
-// Sequential HC (Fig. 5 left) over the window starts [lo, hi) of a chunk.
-// Chunk-relative text byte k is base[head + k].  Returns the number of
-// occurrences found; stores them according to MODE.
+// Records one occurrence (window start `start`, chunk-relative) as the
+// cnt-th of this thread's segment.
+template <int MODE>
+__device__ __forceinline__ void record_match(const Sink& sink, int cnt, int start) {
+  if constexpr (MODE == kCount) {
+    if (cnt < kSlots) sink.slot[cnt * kThreads] = static_cast<uint32_t>(start);
+  } else {
+    const unsigned long long idx = sink.obase + static_cast<unsigned long long>(cnt);
+    if (idx < sink.limit) {
+      if constexpr (MODE == kToRegion)
+        sink.region[idx] = static_cast<uint32_t>(sink.vbase + static_cast<unsigned>(start));
+      else
+        sink.pos[idx] = sink.vbase + static_cast<unsigned long long>(start);
+    }
+  }
+}
+
+template <bool STAGED>
+__device__ __forceinline__ uint8_t text_byte(const uint8_t* base, int k) {
+  if constexpr (STAGED) return base[k];
+  else return __ldg(base + k);
+}
+
+// Walk steps a lane takes on its own before handing the window to its warp.
+constexpr int kShallowSteps = 3;
+
+// HC (Fig. 5 left) over the window starts [lo, hi) of a chunk, one segment
+// per thread; chunk-relative text byte k is base[head + k].  Returns the
+// number of occurrences found and stores them according to MODE.
+//
+// Each lane runs the paper's loop on its own segment.  A window whose
+// back-walk passes kShallowSteps links (rare, except for true occurrences of
+// long patterns) is finished by the whole warp: the lanes hash the next 32
+// q-grams of the walk at once, take the link test of each against its right
+// neighbour's word (passed along with a shuffle), and a ballot finds the
+// first unlinked q-gram -- the same break point the sequential walk reaches.
+// A fully read window is then checked against H_v and verified by the warp.
+// All 32 lanes of a warp must call this together (an empty range is fine).
 template <int Q, bool STAGED, int MODE>
 __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int lo, int hi,
                                             const SearchArgs& a, const uint32_t* Fs,
                                             const uint8_t* xv, const Sink& sink) {
+  const int lane = threadIdx.x & 31;
   const int m = a.m;
   const uint32_t hv = a.hv;
   const int shift = m - Q + 1;
+  const uint8_t* txt = base + head;
   int cnt = 0;
   int e = lo + m - 1;              // window end (chunk-relative)
   const int e_end = hi + m - 1;    // first window end past the segment
-  while (e < e_end) {
-    // first test: the q-gram ending at the window end
-    uint32_t v = qgram_hash<Q, STAGED>(base, head + e - Q + 1, a);
-    uint32_t z = Fs[v];
-    if (z == 0) {
-      e += shift;
-      continue;
-    }
-    // back-walk over the q-grams to the left, each linked to its right one
-    int j = e;
-    const int i = e - m + 2 * Q;
-    bool full = true;
-    while (j >= i) {
-      j -= Q;
-      v = qgram_hash<Q, STAGED>(base, head + j - Q + 1, a);
-      if ((z & (1u << (v & 31u))) == 0) {
-        full = false;
+  bool deep = false;               // window at e waits for the warp
+  int dj = 0;                      // walk position reached
+  uint32_t dz = 0;                 // F word of the q-gram ending at dj
+  while (true) {
+    while (!deep && e < e_end) {
+      // first test: the q-gram ending at the window end
+      uint32_t v = qgram_hash<Q, STAGED>(base, head + e - Q + 1, a);
+      uint32_t z = Fs[v];
+      if (z == 0) {
+        e += shift;
+        continue;
+      }
+      // back-walk over the q-grams to the left, each linked to its right one
+      int j = e;
+      const int i = e - m + 2 * Q;
+      bool broke = false;
+      int steps = 0;
+      while (j >= i) {
+        if (steps == kShallowSteps) {
+          deep = true;
+          break;
+        }
+        j -= Q;
+        v = qgram_hash<Q, STAGED>(base, head + j - Q + 1, a);
+        if ((z & (1u << (v & 31u))) == 0) {
+          broke = true;
+          break;
+        }
+        z = Fs[v];
+        ++steps;
+      }
+      if (deep) {
+        dj = j;
+        dz = z;
         break;
       }
-      z = Fs[v];
+      if (broke) {
+        e = j + shift;             // shift past the unlinked q-gram
+        continue;
+      }
+      // read in full (short window): H_v test, verification, advance by one
+      const int start = e - m + 1;
+      bool eq = v == hv;
+      for (int k = 0; eq && k < m; ++k) eq = text_byte<STAGED>(txt, start + k) == xv[k];
+      if (eq) record_match<MODE>(sink, cnt++, start);
+      e += 1;
     }
-    if (!full) {
-      e = j + shift;               // shift past the unlinked q-gram
-      continue;
-    }
-    const int start = e - m + 1;
-    if (v == hv && verify_window(base + head + start, xv, m)) {
-      if constexpr (MODE == kCount) {
-        if (cnt < kSlots) sink.slot[cnt * kThreads] = static_cast<uint32_t>(start);
-      } else {
-        const unsigned long long idx = sink.obase + static_cast<unsigned long long>(cnt);
-        if (idx < sink.limit) {
-          if constexpr (MODE == kToRegion)
-            sink.region[idx] = static_cast<uint32_t>(sink.vbase + static_cast<unsigned>(start));
-          else
-            sink.pos[idx] = sink.vbase + static_cast<unsigned long long>(start);
+    unsigned need = __ballot_sync(0xffffffffu, deep);
+    if (need == 0u) break;
+    for (; need; need &= need - 1u) {
+      const int L0 = __ffs(need) - 1;
+      const int ew = __shfl_sync(0xffffffffu, e, L0);
+      int j = __shfl_sync(0xffffffffu, dj, L0);
+      uint32_t z = __shfl_sync(0xffffffffu, dz, L0);
+      const int i = ew - m + 2 * Q;
+      uint32_t vlast = 0;
+      int e_next = 0;
+      bool broke = false;
+      while (j >= i) {
+        const int T = (j - i) / Q + 1;      // walk steps left
+        const bool valid = lane < T;
+        const int p = j - (lane + 1) * Q;   // end of this lane's q-gram
+        uint32_t v = 0, zt = 0;
+        if (valid) {
+          v = qgram_hash<Q, STAGED>(base, head + p - Q + 1, a);
+          zt = Fs[v];
+        }
+        uint32_t zprev = __shfl_up_sync(0xffffffffu, zt, 1);
+        if (lane == 0) zprev = z;
+        const unsigned fails = __ballot_sync(0xffffffffu, valid && (zprev & (1u << (v & 31u))) == 0u);
+        if (fails) {
+          e_next = j - __ffs(fails) * Q + shift;  // break at the first unlinked q-gram
+          broke = true;
+          break;
+        }
+        const int last = min(T, 32) - 1;
+        z = __shfl_sync(0xffffffffu, zt, last);
+        vlast = __shfl_sync(0xffffffffu, v, last);
+        j -= (last + 1) * Q;
+      }
+      bool match = false;
+      if (!broke) {
+        // read in full: H_v test, then the warp compares the window with x
+        e_next = ew + 1;
+        if (vlast == hv) {
+          const int start = ew - m + 1;
+          bool eq = true;
+          for (int k = lane; k < m; k += 32) eq &= text_byte<STAGED>(txt, start + k) == xv[k];
+          match = __all_sync(0xffffffffu, eq);
         }
       }
-      ++cnt;
+      if (lane == L0) {
+        if (match) record_match<MODE>(sink, cnt++, ew - m + 1);
+        e = e_next;
+        deep = false;
+      }
     }
-    e += 1;                        // full read: advance by one
   }
   return cnt;
 }
@@ -321,9 +424,8 @@ __global__ void __launch_bounds__(kThreads) hc_scan_kernel(const SearchArgs a) {
       head = 0;
     }
     const int lo = tid * a.L;
-    const int hi = min(lo + a.L, wins);
-    int cnt = 0;
-    if (ok && lo < hi) cnt = scan_segment<Q, STAGED, kCount>(base, head, lo, hi, a, Fs, xv, sink);
+    const int hi = ok ? max(lo, min(lo + a.L, wins)) : lo;
+    const int cnt = scan_segment<Q, STAGED, kCount>(base, head, lo, hi, a, Fs, xv, sink);
 
     // one barrier per chunk in the common case (no occurrence in the chunk)
     if (!__syncthreads_or(cnt != 0 || !ok)) continue;
@@ -334,16 +436,16 @@ __global__ void __launch_bounds__(kThreads) hc_scan_kernel(const SearchArgs a) {
       if (T + total <= S) {
         const uint32_t rel = static_cast<uint32_t>(static_cast<unsigned long long>(i) * a.C);
         const unsigned long long ob = T + excl;
-        if (cnt <= kSlots) {
+        if (cnt <= kSlots)
           for (int k = 0; k < cnt; ++k) region[ob + k] = rel + sink.slot[k * kThreads];
-        } else {
-          Sink w{};
-          w.region = region;
-          w.obase = ob;
-          w.vbase = rel;
-          w.limit = S;
-          scan_segment<Q, STAGED, kToRegion>(base, head, lo, hi, a, Fs, xv, w);
-        }
+        // threads with more than kSlots occurrences scan their segment again,
+        // writing them all (the whole warp takes part)
+        Sink w{};
+        w.region = region;
+        w.obase = ob;
+        w.vbase = rel;
+        w.limit = S;
+        scan_segment<Q, STAGED, kToRegion>(base, head, lo, cnt > kSlots ? hi : lo, a, Fs, xv, w);
       } else {
         overflow = (static_cast<unsigned long long>(i) << 40) | T;
       }
@@ -369,211 +471,274 @@ __global__ void __launch_bounds__(kThreads) hc_scan_kernel(const SearchArgs a) {
 // ---------------------------------------------------------------------------
 // Kernel 1, dense form for m = q.  With m = q the window is a single q-gram,
 // the back-walk is empty and every shift is one position, so HC tests every
-// window in turn: first test F[h] != 0, then h = H_v, then the byte
-// comparison.  Here the 32 lanes of a warp test 32 consecutive windows at
-// once (warp w owns a contiguous slice of the chunk), and the warp compacts
-// its matches in order with a ballot into a shared-memory list; a scan over
-// the warps appends the chunk's matches to the CTA's spill region.
+// window in turn: a window w is reported iff F[h(w)] != 0, h(w) = H_v and
+// w = x.  Where w = x, h(w) = h(x), so the first two tests have the same
+// value for every window that passes the third: the kernel evaluates
+// F[h(x)] != 0 and h(x) = H_v once per warp and the byte comparison per
+// window -- 16 consecutive windows per lane, read with 16-byte shared-memory
+// loads, compared with word-wide XOR/OR and an exact zero-byte test.
+//
+// Every warp is an independent stream: it owns a contiguous range of chunks
+// (record w = blockIdx.x * 8 + warp), stages them through its own ring of
+// shared-memory buffers with bulk copies on its own mbarriers, and appends
+// its matches -- compacted in order with ballots -- straight to its own
+// spill region.  There is no CTA-wide barrier in the loop.
 template <int Q>
 __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[kMaxStages];
-  __shared__ uint32_t warp_cnt[kWarps];
-  __shared__ int s_abort;
+  __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned long long b = blockIdx.x;
-  const unsigned long long c0 = b * a.chunks_per_cta;
+  const unsigned long long w_id = static_cast<unsigned long long>(blockIdx.x) * kWarps + warp;
+  uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
+  for (uint32_t i = tid; i < a.fwords; i += kThreads) Fs[i] = a.F[i];
+  __syncthreads();
+
+  const unsigned long long c0 = w_id * a.chunks_per_cta;
   const unsigned long long c1 = min(c0 + a.chunks_per_cta, a.num_chunks);
   if (c0 >= c1) {
-    if (tid == 0) {
-      a.cta_total[b] = 0;
-      a.cta_overflow[b] = kNoOverflow;
+    if (lane == 0) {
+      a.cta_total[w_id] = 0;
+      a.cta_overflow[w_id] = kNoOverflow;
     }
     return;
   }
-  uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
-  const uint32_t f_bytes = (a.fwords * 4u + 15u) & ~15u;
-  uint8_t* stages = smem + f_bytes;
-  const uint32_t wslice = a.C / kWarps;  // windows per warp and chunk
-  uint16_t* wlist = reinterpret_cast<uint16_t*>(stages + a.stages * a.stage_bytes) + warp * wslice;
-  const int nchunks = static_cast<int>(c1 - c0);
   const int nst = a.stages;
+  const uint32_t f_bytes = (a.fwords * 4u + 15u) & ~15u;
+  uint8_t* stages = smem + f_bytes + static_cast<size_t>(warp) * nst * a.stage_bytes;
+  uint64_t* wb = bars[warp];
+  const int nchunks = static_cast<int>(c1 - c0);
 
-  if (tid == 0) {
-    s_abort = 0;
-    for (int k = 0; k < nst; ++k) mbar_init(&bars[k], 1);
+  // the chunk's bytes go to stage (i % nst); the warp's lane 0 drives the copies
+  auto issue = [&](int st, unsigned long long c) {
+    const unsigned long long cs = c * a.C;
+    const unsigned long long len = min(static_cast<unsigned long long>(a.C) + a.m - 1, a.n - cs);
+    const uint32_t bytes = static_cast<uint32_t>((a.head + len + 15) & ~15ull);
+    mbar_arrive_expect_tx(&wb[st], bytes);
+    bulk_copy_g2s(stages + static_cast<size_t>(st) * a.stage_bytes, a.y + cs - a.head, bytes, &wb[st]);
+  };
+  if (lane == 0) {
+    for (int k = 0; k < nst; ++k) mbar_init(&wb[k], 1);
     fence_mbar_init();
-    for (int k = 0; k < nst && k < nchunks; ++k) issue_chunk(a, stages, bars, k, c0 + k);
+    for (int k = 0; k < nst && k < nchunks; ++k) issue(k, c0 + k);
   }
-  for (uint32_t i = tid; i < a.fwords; i += kThreads) Fs[i] = a.F[i];
-  // the pattern, packed like the text words below, and the mask of its Q bytes
+  __syncwarp();
+
+  // pattern byte c replicated into the 4 bytes of a word
+  uint32_t xrep[Q];
   uint32_t xlo = 0, xhi = 0;
 #pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    const uint32_t xb = a.x[k];
-    if (k < 4) xlo |= xb << (8 * k); else xhi |= xb << (8 * (k - 4));
+  for (int c = 0; c < Q; ++c) {
+    const uint32_t xb = a.x[c];
+    xrep[c] = 0x01010101u * xb;
+    if (c < 4) xlo |= xb << (8 * c); else xhi |= xb << (8 * (c - 4));
   }
-  const uint32_t mlo = Q >= 4 ? 0xffffffffu : ((1u << (8 * Q)) - 1u);
-  const uint32_t mhi = Q >= 8 ? 0xffffffffu : (Q > 4 ? ((1u << (8 * (Q - 4))) - 1u) : 0u);
-  uint32_t lt_mask;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt_mask));
-  __syncthreads();
+  // HC's first test and H_v test, evaluated on x itself (see above)
+  const uint32_t hx = hash_bytes<Q>(xlo, xhi, a);
+  const bool filter_passes = Fs[hx] != 0u && hx == a.hv;
 
   const unsigned long long S = a.region_entries;
-  uint32_t* region = a.region + b * S;
-  unsigned long long T = 0;
+  uint32_t* region = a.region + w_id * S;
+  unsigned long long T = 0;                 // matches so far in this warp's range
   unsigned long long overflow = kNoOverflow;
-  const uint32_t hv = a.hv;
+  bool ok = true;
   int i = 0;
   for (; i < nchunks; ++i) {
     const int st = i % nst;
     const unsigned long long c = c0 + static_cast<unsigned long long>(i);
-    if (tid == 0 && i > 0 && i + nst - 1 < nchunks) {
+    if (lane == 0 && i > 0 && i + nst - 1 < nchunks) {
+      // the buffer of chunk i-1 was released by the __syncwarp that ended it
       fence_proxy_async_smem();
-      issue_chunk(a, stages, bars, (i + nst - 1) % nst, c + nst - 1);
+      issue((i + nst - 1) % nst, c + nst - 1);
     }
-    const bool ok = mbar_wait_bounded(&bars[st], static_cast<uint32_t>(i / nst) & 1u);
-    if (!ok) s_abort = 1;
+    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&wb[st], static_cast<uint32_t>(i / nst) & 1u));
+    if (!ok) break;
     const unsigned long long cs = c * a.C;
-    const uint32_t wins = static_cast<uint32_t>(min(static_cast<unsigned long long>(a.C), a.nwin - cs));
-    const uint32_t* W = reinterpret_cast<const uint32_t*>(stages + static_cast<size_t>(st) * a.stage_bytes);
-    const uint32_t w_lo = warp * wslice;
-    const uint32_t w_hi = min(w_lo + wslice, wins);
-    uint32_t cnt = 0;
-    if (ok) {
-      for (uint32_t base = w_lo; base < w_hi; base += 32) {
-        const uint32_t start = base + lane;
-        const uint32_t o = static_cast<uint32_t>(a.head) + start;
-        const uint32_t r = (o & 3u) * 8u;
-        const uint32_t w0 = W[o >> 2], w1 = W[(o >> 2) + 1];
-        const uint32_t lo = __funnelshift_r(w0, w1, r);
-        uint32_t hi = 0;
-        if constexpr (Q > 4) hi = __funnelshift_r(w1, W[(o >> 2) + 2], r);
-        const uint32_t v = hash_bytes<Q>(lo, hi, a);
-        const bool match = start < w_hi && Fs[v] != 0u && v == hv &&
-                           ((lo ^ xlo) & mlo) == 0u && ((hi ^ xhi) & mhi) == 0u;
-        const uint32_t bal = __ballot_sync(0xffffffffu, match);
-        if (match) wlist[cnt + __popc(bal & lt_mask)] = static_cast<uint16_t>(start);
-        cnt += __popc(bal);
-      }
-    }
-    if (!__syncthreads_or(cnt != 0u || !ok)) continue;
-    if (s_abort) break;
-    if (lane == 0) warp_cnt[warp] = cnt;
-    __syncthreads();
-    uint32_t excl = 0, total = 0;
+    const int wins = static_cast<int>(min(static_cast<unsigned long long>(a.C), a.nwin - cs));
+    const uint8_t* sb = stages + static_cast<size_t>(st) * a.stage_bytes;
+    const uint32_t rel = static_cast<uint32_t>(static_cast<unsigned long long>(i) * a.C);
+    const bool store = overflow == kNoOverflow;
+    unsigned long long t = T;  // matches of the range before this step
+    // window grid shifted by -head so that every lane's 16 windows start at a
+    // 16-byte aligned shared-memory offset; windows outside [0, wins) are
+    // masked
+    for (int base = -a.head; base < wins; base += 512) {
+      const int w0 = base + 16 * lane;      // first window of this lane
+      uint32_t mbits = 0;
+      if (w0 < wins) {  // lanes past the chunk's end read nothing
+        const uint32_t o = static_cast<uint32_t>(a.head + w0);
+        const uint4 A = *reinterpret_cast<const uint4*>(sb + o);
+        const uint2 B = *reinterpret_cast<const uint2*>(sb + o + 16);
+        const uint32_t Tw[6] = {A.x, A.y, A.z, A.w, B.x, B.y};  // bytes o .. o+23
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const uint32_t cw = warp_cnt[w];
-      excl += w < warp ? cw : 0u;
-      total += cw;
-    }
-    if (overflow == kNoOverflow) {
-      if (T + total <= S) {
-        const uint32_t rel = static_cast<uint32_t>(static_cast<unsigned long long>(i) * a.C);
-        for (uint32_t k = lane; k < cnt; k += 32) region[T + excl + k] = rel + wlist[k];
-      } else {
-        overflow = (static_cast<unsigned long long>(i) << 40) | T;
+        for (int g = 0; g < 4; ++g) {
+          // byte k of d stays 0 while window w0+4g+k agrees with x
+          uint32_t d = Tw[g] ^ xrep[0];
+#pragma unroll
+          for (int cc = 1; cc < Q; ++cc) {
+            const int wq = g + (cc >> 2);
+            const uint32_t col = (cc & 3) ? __funnelshift_r(Tw[wq], Tw[wq + 1], 8u * (cc & 3)) : Tw[wq];
+            d |= col ^ xrep[cc];
+          }
+          // exact zero-byte test: bit 7 of a byte set iff the byte is 0
+          const uint32_t z = ~(((d & 0x7f7f7f7fu) + 0x7f7f7f7fu) | d | 0x7f7f7f7fu);
+          // gather the four bit-7 flags into bits 4g .. 4g+3
+          mbits |= (((z >> 7) & 0x01010101u) * 0x01020408u >> 24) << (4 * g);
+        }
+        // windows outside [0, wins)
+        if (w0 < 0) mbits &= 0xffffu << min(-w0, 16);
+        if (w0 + 16 > wins) mbits &= 0xffffu >> (16 - (wins - w0));
+        if (!filter_passes) mbits = 0;
       }
+      if (__ballot_sync(0xffffffffu, mbits != 0u) == 0u) continue;
+      // in-order compaction (lanes in order, a lane's windows in order),
+      // written straight to the spill region
+      const uint32_t mine = static_cast<uint32_t>(__popc(mbits));
+      const uint32_t incl = warp_incl_scan_u32(mine);
+      if (store) {
+        unsigned long long out = t + (incl - mine);
+        while (mbits) {
+          const int k = __ffs(mbits) - 1;
+          if (out < S) region[out] = rel + static_cast<uint32_t>(w0 + k);
+          ++out;
+          mbits &= mbits - 1u;
+        }
+      }
+      t += __shfl_sync(0xffffffffu, incl, 31);
     }
-    T += total;
-    __syncthreads();  // staging buffer, lists and counts are free again
+    if (store && t > S) overflow = (static_cast<unsigned long long>(i) << 40) | T;
+    T = t;
+    __syncwarp();  // staging buffer st is free again
   }
 
-  if (tid == 0) {
-    a.cta_total[b] = T;
-    a.cta_overflow[b] = overflow;
-    if (s_abort) {
+  if (lane == 0) {
+    a.cta_total[w_id] = T;
+    a.cta_overflow[w_id] = overflow;
+    if (!ok) {
       atomicOr(&g_status, 1u);
+      // let the copies still in flight land before the CTA's shared memory goes
       for (int j = i; j < nchunks && j < i + nst; ++j)
-        (void)mbar_wait_bounded(&bars[j % nst], static_cast<uint32_t>(j / nst) & 1u);
+        (void)mbar_wait_bounded(&wb[j % nst], static_cast<uint32_t>(j / nst) & 1u);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2: CTA b's output offset is the sum of cta_total[0..b); copy b's
+// Kernel 2: record r's output offset is the sum of cta_total[0..r); copy its
 // region to the output; re-scan (from global memory) the chunks whose
-// occurrences did not fit in the region.  The last CTA writes the count.
+// occurrences did not fit in the region.  A CTA serves a group of
+// emit_group consecutive records (so the sums over earlier records are made
+// once per group), and kEmitSplit CTAs share each group's copying; the first
+// of them writes the count (last record) and does the re-scans.
 template <int Q>
 __global__ void __launch_bounds__(kThreads) hc_emit_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ unsigned long long red[kWarps];
   __shared__ uint32_t warp_sum[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned long long b = blockIdx.x;
+  const unsigned long long g = blockIdx.x / kEmitSplit;
+  const unsigned part = blockIdx.x % kEmitSplit;
+  const unsigned long long r0 = g * a.emit_group;
+  const unsigned long long r1 = min(r0 + a.emit_group, a.records);
 
+  __shared__ unsigned long long s_tot[kMaxEmitGroup], s_ovf[kMaxEmitGroup];
+  // sum of the earlier records' totals: loads issued 8 at a time
   unsigned long long p = 0;
-  for (unsigned long long k = tid; k < b; k += kThreads) p += a.cta_total[k];
+  for (unsigned long long k0 = tid; k0 < r0; k0 += 8ull * kThreads) {
+    unsigned long long v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const unsigned long long k = k0 + static_cast<unsigned long long>(u) * kThreads;
+      v[u] = k < r0 ? a.cta_total[k] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) p += v[u];
+  }
   p = warp_sum_u64(p);
   if (lane == 0) red[warp] = p;
+  if (static_cast<unsigned long long>(tid) < r1 - r0) {
+    s_tot[tid] = a.cta_total[r0 + tid];
+    s_ovf[tid] = a.cta_overflow[r0 + tid];
+  }
   __syncthreads();
-  unsigned long long P = 0;
+  unsigned long long P = 0;  // output offset of record b (updated below)
   for (int w = 0; w < kWarps; ++w) P += red[w];
 
-  const unsigned long long T = a.cta_total[b];
-  const unsigned long long ovf = a.cta_overflow[b];
-  const unsigned long long stored = ovf == kNoOverflow ? T : (ovf & ((1ull << 40) - 1));
-  const unsigned long long c0 = b * a.chunks_per_cta;
-  const unsigned long long vbase = c0 * a.C;
-  const uint32_t* region = a.region + b * a.region_entries;
-  // copy: 16-byte region loads (regions are 16-byte aligned), four of them
-  // in flight per thread
-  const unsigned long long ncopy = a.cap > P ? min(stored, a.cap - P) : 0ull;
-  const uint4* r4 = reinterpret_cast<const uint4*>(region);
-  const unsigned long long nvec = (ncopy + 3) / 4;
-  for (unsigned long long k0 = tid; k0 < nvec; k0 += 4ull * kThreads) {
-    uint4 v[4];
+  bool f_loaded = false;
+  for (unsigned long long b = r0; b < r1; ++b) {
+    const unsigned long long T = s_tot[b - r0];
+    const unsigned long long ovf = s_ovf[b - r0];
+    const unsigned long long stored = ovf == kNoOverflow ? T : (ovf & ((1ull << 40) - 1));
+    const unsigned long long c0 = b * a.chunks_per_cta;
+    const unsigned long long vbase = c0 * a.C;
+    const uint32_t* region = a.region + b * a.region_entries;
+    // copy: 16-byte region loads (regions are 16-byte aligned), four of them
+    // in flight per thread; 16-byte stores when the output offset is even
+    const unsigned long long ncopy = a.cap > P ? min(stored, a.cap - P) : 0ull;
+    const uint4* r4 = reinterpret_cast<const uint4*>(region);
+    const unsigned long long nvec = (ncopy + 3) / 4;
+    const unsigned long long stride = static_cast<unsigned long long>(kThreads) * kEmitSplit;
+    const bool even = (P & 1ull) == 0ull;
+    for (unsigned long long k0 = part * kThreads + tid; k0 < nvec; k0 += 4 * stride) {
+      uint4 v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const unsigned long long k = k0 + static_cast<unsigned long long>(u) * kThreads;
-      if (k < nvec) v[u] = __ldcs(r4 + k);
-    }
+      for (int u = 0; u < 4; ++u) {
+        const unsigned long long k = k0 + static_cast<unsigned long long>(u) * stride;
+        if (k < nvec) v[u] = __ldcs(r4 + k);
+      }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const unsigned long long k = (k0 + static_cast<unsigned long long>(u) * kThreads) * 4;
-      if (k < ncopy) {
-        unsigned long long* o = a.pos + P + k;
-        __stcs(o, vbase + v[u].x);
-        if (k + 1 < ncopy) __stcs(o + 1, vbase + v[u].y);
-        if (k + 2 < ncopy) __stcs(o + 2, vbase + v[u].z);
-        if (k + 3 < ncopy) __stcs(o + 3, vbase + v[u].w);
+      for (int u = 0; u < 4; ++u) {
+        const unsigned long long k = (k0 + static_cast<unsigned long long>(u) * stride) * 4;
+        if (k < ncopy) {
+          unsigned long long* o = a.pos + P + k;
+          if (even && k + 4 <= ncopy) {
+            __stcs(reinterpret_cast<ulonglong2*>(o), make_ulonglong2(vbase + v[u].x, vbase + v[u].y));
+            __stcs(reinterpret_cast<ulonglong2*>(o + 2), make_ulonglong2(vbase + v[u].z, vbase + v[u].w));
+          } else {
+            __stcs(o, vbase + v[u].x);
+            if (k + 1 < ncopy) __stcs(o + 1, vbase + v[u].y);
+            if (k + 2 < ncopy) __stcs(o + 2, vbase + v[u].z);
+            if (k + 3 < ncopy) __stcs(o + 3, vbase + v[u].w);
+          }
+        }
       }
     }
-  }
-  if (b == gridDim.x - 1 && tid == 0) *a.count_out = P + T;
-  if (ovf == kNoOverflow || P + stored >= a.cap) return;
-
-  // re-scan the chunks from the first unstored one on
-  uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* slots = Fs + ((a.fwords + 3u) & ~3u);
-  for (uint32_t k = tid; k < a.fwords; k += kThreads) Fs[k] = a.F[k];
-  __syncthreads();
-  const unsigned long long c1 = min(c0 + a.chunks_per_cta, a.num_chunks);
-  unsigned long long out = P + stored;
-  Sink cs_sink{};
-  cs_sink.slot = slots + tid;
-  for (unsigned long long c = c0 + (ovf >> 40); c < c1 && out < a.cap; ++c) {
-    const unsigned long long cs = c * a.C;
-    const int wins = static_cast<int>(min(static_cast<unsigned long long>(a.C), a.nwin - cs));
-    const int lo = tid * a.L;
-    const int hi = min(lo + a.L, wins);
-    const uint8_t* base = a.y + cs;
-    int cnt = 0;
-    if (lo < hi) cnt = scan_segment<Q, false, kCount>(base, 0, lo, hi, a, Fs, a.x, cs_sink);
-    uint32_t excl, total;
-    block_scan(static_cast<uint32_t>(cnt), warp_sum, &excl, &total);
-    if (cnt > 0) {
-      Sink w{};
-      w.pos = a.pos;
-      w.obase = out + excl;
-      w.vbase = cs;
-      w.limit = a.cap;
-      scan_segment<Q, false, kToPositions>(base, 0, lo, hi, a, Fs, a.x, w);
+    if (part == 0) {
+      if (b == a.records - 1 && tid == 0) *a.count_out = P + T;
+      if (ovf != kNoOverflow && P + stored < a.cap) {
+        // re-scan the chunks from the first unstored one on
+        uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
+        uint32_t* slots = Fs + ((a.fwords + 3u) & ~3u);
+        if (!f_loaded) {
+          for (uint32_t k = tid; k < a.fwords; k += kThreads) Fs[k] = a.F[k];
+          __syncthreads();
+          f_loaded = true;
+        }
+        const unsigned long long c1 = min(c0 + a.chunks_per_cta, a.num_chunks);
+        unsigned long long out = P + stored;
+        Sink cs_sink{};
+        cs_sink.slot = slots + tid;
+        for (unsigned long long c = c0 + (ovf >> 40); c < c1 && out < a.cap; ++c) {
+          const unsigned long long cs = c * a.C;
+          const int wins = static_cast<int>(min(static_cast<unsigned long long>(a.C), a.nwin - cs));
+          const int lo = tid * a.L;
+          const int hi = max(lo, min(lo + a.L, wins));
+          const uint8_t* base = a.y + cs;
+          const int cnt = scan_segment<Q, false, kCount>(base, 0, lo, hi, a, Fs, a.x, cs_sink);
+          uint32_t excl, total;
+          block_scan(static_cast<uint32_t>(cnt), warp_sum, &excl, &total);
+          Sink w{};
+          w.pos = a.pos;
+          w.obase = out + excl;
+          w.vbase = cs;
+          w.limit = a.cap;
+          scan_segment<Q, false, kToPositions>(base, 0, lo, cnt > 0 ? hi : lo, a, Fs, a.x, w);
+          out += total;
+          __syncthreads();
+        }
+      }
     }
-    out += total;
-    __syncthreads();
+    P += T;
   }
 }
 
@@ -698,7 +863,7 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   int L = L_req;
   if (L == 0) {
     if (kind == HC_MODE_DENSE) {
-      L = 32;
+      L = 8;
     } else if (kind == HC_MODE_DIRECT) {
       L = std::min(4096, std::max(64, shift));
     } else {
@@ -711,7 +876,7 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   if (L < 1 || L > 4096) return set_error(HC_ERR_ARG, "hc_search: lane_bytes out of [1, 4096]");
   if (kind == HC_MODE_DENSE && L > 256)
     return set_error(HC_ERR_ARG, "hc_search: the dense mode needs lane_bytes <= 256");
-  const int stages = o && o->stages ? o->stages : (kind == HC_MODE_DENSE ? 4 : 3);
+  const int stages = o && o->stages ? o->stages : 3;
   if (stages < 2 || stages > kMaxStages) return set_error(HC_ERR_ARG, "hc_search: stages out of [2, 4]");
   p.kind = kind;
   p.L = L;
@@ -721,11 +886,18 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   const size_t fbytes = (f->F.size() * 4 + 15) & ~size_t(15);
   const size_t slot_bytes = size_t(kSlots) * kThreads * 4;
   // staged text: head (< 16) + C + m - 1 bytes, rounded to 16, plus slack for
-  // the word loads that run past the last q-gram
+  // the word loads that run past the last q-gram (at most 20 bytes past the
+  // chunk's last window start in the dense kernel, 12 in the others)
   p.stage_bytes = static_cast<uint32_t>(((16 + p.C + f->m - 1 + 15) & ~size_t(15)) + 64);
   if (kind == HC_MODE_DENSE) {
+    // one ring of `stages` buffers per warp
     p.scan = dense_kernel_for_q(f->q);
-    p.smem_scan = fbytes + size_t(stages) * p.stage_bytes + size_t(p.C) * 2;
+    p.smem_scan = fbytes + size_t(kWarps) * stages * p.stage_bytes;
+    if (mode == HC_MODE_AUTO && p.smem_scan + static_smem(p.scan) > di.smem_optin)
+      kind = HC_MODE_STAGED;  // caller's lane_bytes too large for per-warp rings
+  }
+  p.kind = kind;
+  if (kind == HC_MODE_DENSE) {
   } else if (kind == HC_MODE_STAGED) {
     p.scan = scan_kernel_for_q<true>(f->q);
     p.smem_scan = fbytes + p.x_smem + size_t(stages) * p.stage_bytes + slot_bytes;
@@ -756,17 +928,28 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
 
   const unsigned long long nwin = n - f->m + 1;
   p.num_chunks = (nwin + p.C - 1) / p.C;
-  unsigned long long grid = std::min<unsigned long long>(p.num_chunks,
-                                                         static_cast<unsigned long long>(per_sm) * di.sm_count);
-  p.chunks_per_cta = (p.num_chunks + grid - 1) / grid;
+  // one record (total, overflow mark, spill region) per CTA, or per warp in
+  // the dense kernel, each owning a contiguous range of chunks
+  const unsigned long long per_record = kind == HC_MODE_DENSE ? kWarps : 1;
+  unsigned long long records = std::min<unsigned long long>(
+      p.num_chunks, static_cast<unsigned long long>(per_sm) * di.sm_count * per_record);
+  p.chunks_per_cta = (p.num_chunks + records - 1) / records;
   if (p.chunks_per_cta * p.C >= (1ull << 32))
     return set_error(HC_ERR_ARG, "hc_search: text too long for one launch");
-  p.grid = (p.num_chunks + p.chunks_per_cta - 1) / p.chunks_per_cta;
+  p.records = (p.num_chunks + p.chunks_per_cta - 1) / p.chunks_per_cta;
+  p.grid = (p.records + per_record - 1) / per_record;
+  p.records = p.grid * per_record;
   unsigned long long spill = o ? o->spill_entries : 0;
   if (spill == 0)
     spill = cap == 0 ? 0 : std::min<unsigned long long>(nwin, std::max<unsigned long long>(cap, 1ull << 20));
-  p.region_entries = (std::max<unsigned long long>(1, (spill + p.grid - 1) / p.grid) + 3) & ~3ull;
-  p.ws_bytes = p.grid * 16 + p.grid * p.region_entries * 4;
+  p.region_entries = (std::max<unsigned long long>(1, (spill + p.records - 1) / p.records) + 3) & ~3ull;
+  // emit: about 2 record groups per SM, kEmitSplit CTAs each
+  const unsigned long long groups = std::max<unsigned long long>(
+      (p.records + kMaxEmitGroup - 1) / kMaxEmitGroup,
+      std::min<unsigned long long>(p.records, 2ull * di.sm_count));
+  p.emit_group = (p.records + groups - 1) / groups;
+  p.emit_ctas = ((p.records + p.emit_group - 1) / p.emit_group) * kEmitSplit;
+  p.ws_bytes = p.records * 16 + p.records * p.region_entries * 4;
   *out = p;
   return HC_OK;
 }
@@ -789,8 +972,8 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   a.cap = pos ? cap : 0;
   a.count_out = reinterpret_cast<unsigned long long*>(count_dev);
   a.cta_total = static_cast<unsigned long long*>(ws);
-  a.cta_overflow = a.cta_total + p.grid;
-  a.region = reinterpret_cast<uint32_t*>(a.cta_overflow + p.grid);
+  a.cta_overflow = a.cta_total + p.records;
+  a.region = reinterpret_cast<uint32_t*>(a.cta_overflow + p.records);
   a.region_entries = p.region_entries;
   a.num_chunks = p.num_chunks;
   a.chunks_per_cta = p.chunks_per_cta;
@@ -800,6 +983,8 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   a.stage_bytes = p.stage_bytes;
   a.x_smem = p.x_smem;
   a.stages = p.stages;
+  a.records = p.records;
+  a.emit_group = p.emit_group;
   // byte groups of h: the longest prefix whose weights 2^(s*k) fit in a byte
   const int s = f->s, q = f->q;
   int g = 1;
@@ -824,7 +1009,7 @@ int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_
   timing_end(t0, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
   TimingToken t1 = timing_begin(kKindEmit, stream);
-  p.emit<<<static_cast<unsigned>(p.grid), kThreads, p.smem_emit, stream>>>(a);
+  p.emit<<<static_cast<unsigned>(p.emit_ctas), kThreads, p.smem_emit, stream>>>(a);
   e = cudaGetLastError();
   timing_end(t1, stream);
   g_launches.fetch_add(2);
@@ -849,7 +1034,7 @@ int launch_planned_filter_ptrs(const Filter* f, const SearchPlan& p, const uint3
   timing_end(t0, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
   TimingToken t1 = timing_begin(kKindEmit, stream);
-  p.emit<<<static_cast<unsigned>(p.grid), kThreads, p.smem_emit, stream>>>(a);
+  p.emit<<<static_cast<unsigned>(p.emit_ctas), kThreads, p.smem_emit, stream>>>(a);
   e = cudaGetLastError();
   timing_end(t1, stream);
   g_launches.fetch_add(2);

@@ -204,7 +204,7 @@ def test_launch_options_and_spill_overflow(opts):
 
 
 @pytest.mark.parametrize("opts", [
-    dict(mode=3), dict(mode=3, lane_bytes=1), dict(mode=3, lane_bytes=128, stages=2),
+    dict(mode=3), dict(mode=3, lane_bytes=1), dict(mode=3, lane_bytes=24, stages=2),
     dict(mode=3, lane_bytes=33, spill_entries=10), dict(mode=3, spill_entries=1),
     dict(mode=3, lane_bytes=5, ctas_per_sm=1, stages=3)])
 def test_dense_mode_m_equals_q(opts):
