@@ -131,7 +131,12 @@ int hc_search_async(const hc_filter *f, const uint8_t *y_dev, size_t n,
  *   spill_entries: capacity, in positions, of the per-launch spill regions
  *         that hold occurrences until their output offsets are known
  *         (positions that do not fit are found again by a second scan of
- *         the affected chunks).
+ *         the affected chunks);
+ *   speculate: 1 -- in the staged and direct modes, the lanes of a warp
+ *         test the next 32 windows of HC's miss sequence together and
+ *         finish the first one that hits, with the warp; -1 -- each lane
+ *         runs HC over its own run of window starts; 0 -- automatic (the
+ *         per-lane form, faster on every workload measured so far).
  * struct_size must be sizeof(hc_search_opts). */
 enum { HC_MODE_AUTO = 0, HC_MODE_STAGED = 1, HC_MODE_DIRECT = 2, HC_MODE_DENSE = 3 };
 
@@ -142,6 +147,8 @@ typedef struct hc_search_opts {
     int ctas_per_sm;
     int mode;
     uint64_t spill_entries;
+    int speculate;
+    int reserved;
 } hc_search_opts;
 
 /* hc_search_ex: hc_search_async with explicit launch options (opts may be

@@ -99,6 +99,7 @@ struct SearchPlan {
   unsigned long long num_chunks = 0, chunks_per_cta = 0, grid = 0, region_entries = 0;
   unsigned long long records = 0;  // spill records: one per CTA (one per warp when dense)
   unsigned long long emit_group = 0, emit_ctas = 0;  // emit kernel: records per CTA group, CTAs
+  bool spec = false;              // warp-speculative HC (staged/direct kinds)
   size_t ws_bytes = 0;            // workspace bytes (device), no zeroing needed
 };
 

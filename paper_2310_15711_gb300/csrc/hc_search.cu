@@ -51,7 +51,7 @@ constexpr int kMaxSmemX = 4096;             // larger patterns verify from globa
 constexpr size_t kMaxStagedM = 16384;       // larger patterns use the unstaged kernel
 constexpr unsigned long long kNoOverflow = ~0ull;
 constexpr int kDirectShift = 200;
-constexpr int kEmitSplit = 4;               // CTAs of the emit kernel per record group
+constexpr int kEmitSplit = 2;               // CTAs of the emit kernel per record group
 constexpr int kMaxEmitGroup = 64;           // records per emit record group, at most           // shifts this long skip most 32-byte sectors
 
 // bit 0: a bounded device-side wait gave up
@@ -83,7 +83,8 @@ struct SearchArgs {
   uint32_t stage_bytes;      // bytes per staging buffer (16-byte multiple)
   uint32_t x_smem;           // bytes of shared memory for x (0: verify from global)
   int stages;                // staging buffers per CTA (2..kMaxStages)
-  unsigned long long records;     // spill records (per CTA, or per warp when dense)
+  unsigned long long records;     // spill records (one per warp)
+  int spec;                       // 1: warp-speculative HC per chunk (rare first-test hits)
   unsigned long long emit_group;  // records served by one emit CTA group
   // h as at most two byte-dot-products (see qgram_hash): bytes [0, g0) with
   // weights w0, bytes [g0, q) with weights w1, scaled by 2^(s*g0)
@@ -191,6 +192,98 @@ __device__ __forceinline__ uint8_t text_byte(const uint8_t* base, int k) {
   else return __ldg(base + k);
 }
 
+// Finishes the HC test of the window ending at ew with the whole warp: the
+// back-walk has reached q-gram end j, whose F word is z, with every link so
+// far passing; vlast is the hash of that q-gram.  The lanes hash the next 32
+// q-grams of the walk at once; lane t checks the link of q-gram t against
+// the word of q-gram t-1 (passed along with a shuffle); a ballot finds the
+// first unlinked q-gram, which is where the sequential walk would break.  A
+// window read in full is checked against H_v and compared with x by the
+// warp.  Returns the next window end; *match tells whether the window is an
+// occurrence.  All 32 lanes must call it with the same arguments.
+template <int Q, bool STAGED>
+__device__ __forceinline__ int warp_finish_window(const uint8_t* base, int head, int ew, int j,
+                                                  uint32_t z, uint32_t vlast, const SearchArgs& a,
+                                                  const uint32_t* Fs, const uint8_t* xv,
+                                                  bool* match) {
+  const int lane = threadIdx.x & 31;
+  const int m = a.m;
+  const int shift = m - Q + 1;
+  const int i = ew - m + 2 * Q;
+  *match = false;
+  while (j >= i) {
+    const int T = (j - i) / Q + 1;      // walk steps left
+    const bool valid = lane < T;
+    const int p = j - (lane + 1) * Q;   // end of this lane's q-gram
+    uint32_t v = 0, zt = 0;
+    if (valid) {
+      v = qgram_hash<Q, STAGED>(base, head + p - Q + 1, a);
+      zt = Fs[v];
+    }
+    uint32_t zprev = __shfl_up_sync(0xffffffffu, zt, 1);
+    if (lane == 0) zprev = z;
+    const unsigned fails = __ballot_sync(0xffffffffu, valid && (zprev & (1u << (v & 31u))) == 0u);
+    if (fails) return j - __ffs(fails) * Q + shift;  // shift past the unlinked q-gram
+    const int last = min(T, 32) - 1;
+    z = __shfl_sync(0xffffffffu, zt, last);
+    vlast = __shfl_sync(0xffffffffu, v, last);
+    j -= (last + 1) * Q;
+  }
+  // read in full: H_v test, then the warp compares the window with x
+  if (vlast == a.hv) {
+    const int start = ew - m + 1;
+    const uint8_t* txt = base + head;
+    bool eq = true;
+    for (int k = lane; k < m; k += 32) eq &= text_byte<STAGED>(txt, start + k) == xv[k];
+    *match = __all_sync(0xffffffffu, eq);
+  }
+  return ew + 1;
+}
+
+// HC over all window starts [0, wins) of a chunk by one warp, for patterns
+// whose first test rarely hits: the lanes test the next 32 windows of the
+// miss sequence e, e+S, ..., e+31S (S = m-q+1) at once; a ballot finds the
+// first whose end q-gram hits a non-empty word of F -- every window before
+// it is a miss that the sequential loop would visit and shift past -- and
+// the warp finishes that window (warp_finish_window) and resumes after it.
+// Occurrences are appended in order at sink.obase + count.  Returns the
+// number found.  All 32 lanes must call it together.
+template <int Q, bool STAGED, int MODE>
+__device__ __forceinline__ int warp_scan_chunk(const uint8_t* base, int head, int wins,
+                                               const SearchArgs& a, const uint32_t* Fs,
+                                               const uint8_t* xv, const Sink& sink) {
+  const int lane = threadIdx.x & 31;
+  const int m = a.m;
+  const int shift = m - Q + 1;
+  const int e_end = wins + m - 1;
+  int cnt = 0;
+  int e = m - 1;
+  while (e < e_end) {
+    const int ek = e + lane * shift;
+    const bool valid = ek < e_end;
+    uint32_t v = 0, z = 0;
+    if (valid) {
+      v = qgram_hash<Q, STAGED>(base, head + ek - Q + 1, a);
+      z = Fs[v];
+    }
+    const unsigned hits = __ballot_sync(0xffffffffu, z != 0u);
+    if (hits == 0u) {
+      e += 32 * shift;
+      continue;
+    }
+    const int k = __ffs(hits) - 1;
+    const int ew = e + k * shift;
+    bool match;
+    e = warp_finish_window<Q, STAGED>(base, head, ew, ew, __shfl_sync(0xffffffffu, z, k),
+                                      __shfl_sync(0xffffffffu, v, k), a, Fs, xv, &match);
+    if (match) {
+      if (lane == 0) record_match<MODE>(sink, cnt, ew - m + 1);
+      ++cnt;
+    }
+  }
+  return cnt;
+}
+
 // Walk steps a lane takes on its own before handing the window to its warp.
 constexpr int kShallowSteps = 3;
 
@@ -270,45 +363,10 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
     for (; need; need &= need - 1u) {
       const int L0 = __ffs(need) - 1;
       const int ew = __shfl_sync(0xffffffffu, e, L0);
-      int j = __shfl_sync(0xffffffffu, dj, L0);
-      uint32_t z = __shfl_sync(0xffffffffu, dz, L0);
-      const int i = ew - m + 2 * Q;
-      uint32_t vlast = 0;
-      int e_next = 0;
-      bool broke = false;
-      while (j >= i) {
-        const int T = (j - i) / Q + 1;      // walk steps left
-        const bool valid = lane < T;
-        const int p = j - (lane + 1) * Q;   // end of this lane's q-gram
-        uint32_t v = 0, zt = 0;
-        if (valid) {
-          v = qgram_hash<Q, STAGED>(base, head + p - Q + 1, a);
-          zt = Fs[v];
-        }
-        uint32_t zprev = __shfl_up_sync(0xffffffffu, zt, 1);
-        if (lane == 0) zprev = z;
-        const unsigned fails = __ballot_sync(0xffffffffu, valid && (zprev & (1u << (v & 31u))) == 0u);
-        if (fails) {
-          e_next = j - __ffs(fails) * Q + shift;  // break at the first unlinked q-gram
-          broke = true;
-          break;
-        }
-        const int last = min(T, 32) - 1;
-        z = __shfl_sync(0xffffffffu, zt, last);
-        vlast = __shfl_sync(0xffffffffu, v, last);
-        j -= (last + 1) * Q;
-      }
-      bool match = false;
-      if (!broke) {
-        // read in full: H_v test, then the warp compares the window with x
-        e_next = ew + 1;
-        if (vlast == hv) {
-          const int start = ew - m + 1;
-          bool eq = true;
-          for (int k = lane; k < m; k += 32) eq &= text_byte<STAGED>(txt, start + k) == xv[k];
-          match = __all_sync(0xffffffffu, eq);
-        }
-      }
+      const int j = __shfl_sync(0xffffffffu, dj, L0);
+      const uint32_t z = __shfl_sync(0xffffffffu, dz, L0);
+      bool match;
+      const int e_next = warp_finish_window<Q, STAGED>(base, head, ew, j, z, 0u, a, Fs, xv, &match);
       if (lane == L0) {
         if (match) record_match<MODE>(sink, cnt++, ew - m + 1);
         e = e_next;
@@ -337,80 +395,80 @@ __device__ __forceinline__ void block_scan(uint32_t cnt, uint32_t* warp_sum, uin
   *total = warp_sum[kWarps - 1];
 }
 
-// Starts the bulk copy of chunk c's text into staging buffer `st`.
-__device__ __forceinline__ void issue_chunk(const SearchArgs& a, uint8_t* stages, uint64_t* bars,
-                                            int st, unsigned long long c) {
-  const unsigned long long cs = c * a.C;
-  const unsigned long long len = min(static_cast<unsigned long long>(a.C) + a.m - 1, a.n - cs);
-  const uint32_t bytes = static_cast<uint32_t>((a.head + len + 15) & ~15ull);
-  const uint8_t* src = a.y + cs - a.head;  // 16-byte aligned: C is a multiple of 16
-  mbar_arrive_expect_tx(&bars[st], bytes);
-  bulk_copy_g2s(stages + static_cast<size_t>(st) * a.stage_bytes, src, bytes, &bars[st]);
-}
-
 // ---------------------------------------------------------------------------
-// Kernel 1: HC over CTA b's contiguous range of chunks; occurrences go to
-// b's spill region in text order; the total to cta_total[b].
+// Kernel 1: per-lane HC.  Every warp is an independent stream: record
+// w = blockIdx.x * 8 + warp owns a contiguous range of chunks of 32*L window
+// starts; lane l scans starts [lL, lL + L) of each chunk.  Staged: the warp
+// brings its chunks into its own ring of shared-memory buffers with bulk
+// copies on its own mbarriers; direct: the lanes read the text from global
+// memory.  Occurrences go, in text order, to the warp's spill region; the
+// total to cta_total[w].  No CTA-wide barrier in the loop.
 template <int Q, bool STAGED>
 __global__ void __launch_bounds__(kThreads) hc_scan_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[kMaxStages];
-  __shared__ uint32_t warp_sum[kWarps];
-  __shared__ int s_abort;
+  __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
 
-  const int tid = threadIdx.x;
-  const unsigned long long b = blockIdx.x;
-  const unsigned long long c0 = b * a.chunks_per_cta;
-  const unsigned long long c1 = min(c0 + a.chunks_per_cta, a.num_chunks);
-  if (c0 >= c1) {
-    if (tid == 0) {
-      a.cta_total[b] = 0;
-      a.cta_overflow[b] = kNoOverflow;
-    }
-    return;
-  }
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned long long w_id = static_cast<unsigned long long>(blockIdx.x) * kWarps + warp;
   uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
   const uint32_t f_bytes = (a.fwords * 4u + 15u) & ~15u;
   uint8_t* xs = smem + f_bytes;
-  uint8_t* stages = xs + a.x_smem;
-  uint32_t* slots =
-      reinterpret_cast<uint32_t*>(stages + (STAGED ? a.stages * a.stage_bytes : 0u));
-  const int nchunks = static_cast<int>(c1 - c0);
-  const int nst = a.stages;
-
-  if (tid == 0) {
-    s_abort = 0;
-    if constexpr (STAGED) {
-      for (int k = 0; k < nst; ++k) mbar_init(&bars[k], 1);
-      fence_mbar_init();
-      for (int k = 0; k < nst && k < nchunks; ++k) issue_chunk(a, stages, bars, k, c0 + k);
-    }
-  }
+  uint32_t* slots = reinterpret_cast<uint32_t*>(xs + a.x_smem);
   for (uint32_t i = tid; i < a.fwords; i += kThreads) Fs[i] = a.F[i];
   for (uint32_t i = tid; i < a.x_smem && i < static_cast<uint32_t>(a.m); i += kThreads)
     xs[i] = a.x[i];
   const uint8_t* xv = a.x_smem ? xs : a.x;
   __syncthreads();
 
+  const unsigned long long c0 = w_id * a.chunks_per_cta;
+  const unsigned long long c1 = min(c0 + a.chunks_per_cta, a.num_chunks);
+  if (c0 >= c1) {
+    if (lane == 0) {
+      a.cta_total[w_id] = 0;
+      a.cta_overflow[w_id] = kNoOverflow;
+    }
+    return;
+  }
+  const int nchunks = static_cast<int>(c1 - c0);
+  const int nst = a.stages;
+  uint8_t* stages = reinterpret_cast<uint8_t*>(slots + kSlots * kThreads) +
+                    static_cast<size_t>(warp) * nst * a.stage_bytes;
+  uint64_t* wb = bars[warp];
+  auto issue = [&](int st, unsigned long long c) {
+    const unsigned long long cs = c * a.C;
+    const unsigned long long len = min(static_cast<unsigned long long>(a.C) + a.m - 1, a.n - cs);
+    const uint32_t bytes = static_cast<uint32_t>((a.head + len + 15) & ~15ull);
+    mbar_arrive_expect_tx(&wb[st], bytes);
+    bulk_copy_g2s(stages + static_cast<size_t>(st) * a.stage_bytes, a.y + cs - a.head, bytes, &wb[st]);
+  };
+  if constexpr (STAGED) {
+    if (lane == 0) {
+      for (int k = 0; k < nst; ++k) mbar_init(&wb[k], 1);
+      fence_mbar_init();
+      for (int k = 0; k < nst && k < nchunks; ++k) issue(k, c0 + k);
+    }
+    __syncwarp();
+  }
+
   const unsigned long long S = a.region_entries;
-  uint32_t* region = a.region + b * S;
+  uint32_t* region = a.region + w_id * S;
   unsigned long long T = 0;               // occurrences so far in this range
   unsigned long long overflow = kNoOverflow;
   Sink sink{};
   sink.slot = slots + tid;
+  bool ok = true;
   int i = 0;
   for (; i < nchunks; ++i) {
     const int st = i % nst;
     const unsigned long long c = c0 + static_cast<unsigned long long>(i);
-    bool ok = true;
     if constexpr (STAGED) {
-      if (tid == 0 && i > 0 && i + nst - 1 < nchunks) {
-        // the buffer of chunk i-1 was released by the barrier that ended it
+      if (lane == 0 && i > 0 && i + nst - 1 < nchunks) {
+        // the buffer of chunk i-1 was released by the __syncwarp that ended it
         fence_proxy_async_smem();
-        issue_chunk(a, stages, bars, (i + nst - 1) % nst, c + nst - 1);
+        issue((i + nst - 1) % nst, c + nst - 1);
       }
-      ok = mbar_wait_bounded(&bars[st], static_cast<uint32_t>(i / nst) & 1u);
-      if (!ok) s_abort = 1;
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&wb[st], static_cast<uint32_t>(i / nst) & 1u));
+      if (!ok) break;
     }
     const unsigned long long cs = c * a.C;
     const int wins = static_cast<int>(min(static_cast<unsigned long long>(a.C), a.nwin - cs));
@@ -423,46 +481,60 @@ __global__ void __launch_bounds__(kThreads) hc_scan_kernel(const SearchArgs a) {
       base = a.y + cs;
       head = 0;
     }
-    const int lo = tid * a.L;
-    const int hi = ok ? max(lo, min(lo + a.L, wins)) : lo;
+    if (a.spec) {
+      // warp-speculative HC over the whole chunk; matches appended in order
+      Sink w{};
+      w.region = region;
+      w.obase = T;
+      w.vbase = static_cast<uint32_t>(static_cast<unsigned long long>(i) * a.C);
+      w.limit = overflow == kNoOverflow ? S : 0ull;
+      const unsigned long long found =
+          static_cast<unsigned long long>(warp_scan_chunk<Q, STAGED, kToRegion>(base, head, wins, a, Fs, xv, w));
+      if (overflow == kNoOverflow && T + found > S) overflow = (static_cast<unsigned long long>(i) << 40) | T;
+      T += found;
+      __syncwarp();
+      continue;
+    }
+    const int lo = lane * a.L;
+    const int hi = max(lo, min(lo + a.L, wins));
     const int cnt = scan_segment<Q, STAGED, kCount>(base, head, lo, hi, a, Fs, xv, sink);
 
-    // one barrier per chunk in the common case (no occurrence in the chunk)
-    if (!__syncthreads_or(cnt != 0 || !ok)) continue;
-    if (s_abort) break;
-    uint32_t excl, total;
-    block_scan(static_cast<uint32_t>(cnt), warp_sum, &excl, &total);
-    if (overflow == kNoOverflow) {
-      if (T + total <= S) {
-        const uint32_t rel = static_cast<uint32_t>(static_cast<unsigned long long>(i) * a.C);
-        const unsigned long long ob = T + excl;
-        if (cnt <= kSlots)
-          for (int k = 0; k < cnt; ++k) region[ob + k] = rel + sink.slot[k * kThreads];
-        // threads with more than kSlots occurrences scan their segment again,
-        // writing them all (the whole warp takes part)
-        Sink w{};
-        w.region = region;
-        w.obase = ob;
-        w.vbase = rel;
-        w.limit = S;
-        scan_segment<Q, STAGED, kToRegion>(base, head, lo, cnt > kSlots ? hi : lo, a, Fs, xv, w);
-      } else {
-        overflow = (static_cast<unsigned long long>(i) << 40) | T;
+    if (__any_sync(0xffffffffu, cnt != 0)) {
+      const uint32_t incl = warp_incl_scan_u32(static_cast<uint32_t>(cnt));
+      const uint32_t excl = incl - static_cast<uint32_t>(cnt);
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      if (overflow == kNoOverflow) {
+        if (T + total <= S) {
+          const uint32_t rel = static_cast<uint32_t>(static_cast<unsigned long long>(i) * a.C);
+          const unsigned long long ob = T + excl;
+          if (cnt <= kSlots)
+            for (int k = 0; k < cnt; ++k) region[ob + k] = rel + sink.slot[k * kThreads];
+          // lanes with more than kSlots occurrences scan their segment again,
+          // writing them all (the whole warp takes part)
+          Sink w{};
+          w.region = region;
+          w.obase = ob;
+          w.vbase = rel;
+          w.limit = S;
+          scan_segment<Q, STAGED, kToRegion>(base, head, lo, cnt > kSlots ? hi : lo, a, Fs, xv, w);
+        } else {
+          overflow = (static_cast<unsigned long long>(i) << 40) | T;
+        }
       }
+      T += total;
     }
-    T += total;
-    __syncthreads();  // staging buffer, slots and warp_sum are free again
+    __syncwarp();  // staging buffer st and the slots are free again
   }
 
-  if (tid == 0) {
-    a.cta_total[b] = T;
-    a.cta_overflow[b] = overflow;
-    if (s_abort) {
-      atomicOr(&g_status, 1u);
-      if constexpr (STAGED) {
+  if (lane == 0) {
+    a.cta_total[w_id] = T;
+    a.cta_overflow[w_id] = overflow;
+    if constexpr (STAGED) {
+      if (!ok) {
+        atomicOr(&g_status, 1u);
         // let the copies still in flight land before the CTA's shared memory goes
         for (int j = i; j < nchunks && j < i + nst; ++j)
-          (void)mbar_wait_bounded(&bars[j % nst], static_cast<uint32_t>(j / nst) & 1u);
+          (void)mbar_wait_bounded(&wb[j % nst], static_cast<uint32_t>(j / nst) & 1u);
       }
     }
   }
@@ -668,6 +740,8 @@ __global__ void __launch_bounds__(kThreads) hc_emit_kernel(const SearchArgs a) {
   for (unsigned long long b = r0; b < r1; ++b) {
     const unsigned long long T = s_tot[b - r0];
     const unsigned long long ovf = s_ovf[b - r0];
+    if (part == 0 && b == a.records - 1 && tid == 0) *a.count_out = P + T;
+    if (T == 0) continue;  // nothing to copy, nothing overflowed
     const unsigned long long stored = ovf == kNoOverflow ? T : (ovf & ((1ull << 40) - 1));
     const unsigned long long c0 = b * a.chunks_per_cta;
     const unsigned long long vbase = c0 * a.C;
@@ -704,7 +778,6 @@ __global__ void __launch_bounds__(kThreads) hc_emit_kernel(const SearchArgs a) {
       }
     }
     if (part == 0) {
-      if (b == a.records - 1 && tid == 0) *a.count_out = P + T;
       if (ovf != kNoOverflow && P + stored < a.cap) {
         // re-scan the chunks from the first unstored one on
         uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
@@ -876,11 +949,14 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   if (L < 1 || L > 4096) return set_error(HC_ERR_ARG, "hc_search: lane_bytes out of [1, 4096]");
   if (kind == HC_MODE_DENSE && L > 256)
     return set_error(HC_ERR_ARG, "hc_search: the dense mode needs lane_bytes <= 256");
-  const int stages = o && o->stages ? o->stages : 3;
+  const int stages = o && o->stages ? o->stages : (kind == HC_MODE_STAGED ? 2 : 3);
   if (stages < 2 || stages > kMaxStages) return set_error(HC_ERR_ARG, "hc_search: stages out of [2, 4]");
   p.kind = kind;
   p.L = L;
-  p.C = static_cast<uint32_t>(kThreads) * static_cast<uint32_t>(L);
+  // a chunk holds 256*L window starts in the dense kernel (a warp covers it in
+  // L/2 steps of 16 windows per lane) and 32*L otherwise (one segment of L
+  // starts per lane of the warp that owns it)
+  p.C = static_cast<uint32_t>(kind == HC_MODE_DENSE ? kThreads : 32) * static_cast<uint32_t>(L);
   p.stages = stages;
   p.x_smem = f->m <= static_cast<size_t>(kMaxSmemX) ? static_cast<uint32_t>((f->m + 15) & ~size_t(15)) : 0u;
   const size_t fbytes = (f->F.size() * 4 + 15) & ~size_t(15);
@@ -893,14 +969,16 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
     // one ring of `stages` buffers per warp
     p.scan = dense_kernel_for_q(f->q);
     p.smem_scan = fbytes + size_t(kWarps) * stages * p.stage_bytes;
-    if (mode == HC_MODE_AUTO && p.smem_scan + static_smem(p.scan) > di.smem_optin)
+    if (mode == HC_MODE_AUTO && p.smem_scan + static_smem(p.scan) > di.smem_optin) {
       kind = HC_MODE_STAGED;  // caller's lane_bytes too large for per-warp rings
+      p.C = 32u * static_cast<uint32_t>(L);
+      p.stage_bytes = static_cast<uint32_t>(((16 + p.C + f->m - 1 + 15) & ~size_t(15)) + 64);
+    }
   }
   p.kind = kind;
-  if (kind == HC_MODE_DENSE) {
-  } else if (kind == HC_MODE_STAGED) {
+  if (kind == HC_MODE_STAGED) {
     p.scan = scan_kernel_for_q<true>(f->q);
-    p.smem_scan = fbytes + p.x_smem + size_t(stages) * p.stage_bytes + slot_bytes;
+    p.smem_scan = fbytes + p.x_smem + slot_bytes + size_t(kWarps) * stages * p.stage_bytes;
     if (p.smem_scan + static_smem(p.scan) > di.smem_optin) {
       if (mode == HC_MODE_STAGED)
         return set_error(HC_ERR_ARG, "hc_search: staging buffers exceed shared memory");
@@ -915,6 +993,10 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
     return set_error(HC_ERR_ARG, "hc_search: filter and buffers exceed shared memory");
   p.emit = emit_kernel_for_q(f->q);
   p.smem_emit = (((f->F.size() + 3) & ~size_t(3)) * 4) + slot_bytes;
+  // warp-speculative HC only on request: measured on GB300 it loses to the
+  // per-lane form on every sweep cell (each first-test hit serialises the
+  // warp), so the automatic choice is the per-lane form
+  if (kind != HC_MODE_DENSE) p.spec = o != nullptr && o->speculate > 0;
 
   int rc = ensure_smem_attr(dev, p.scan, p.smem_scan);
   if (rc != HC_OK) return rc;
@@ -928,9 +1010,9 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
 
   const unsigned long long nwin = n - f->m + 1;
   p.num_chunks = (nwin + p.C - 1) / p.C;
-  // one record (total, overflow mark, spill region) per CTA, or per warp in
-  // the dense kernel, each owning a contiguous range of chunks
-  const unsigned long long per_record = kind == HC_MODE_DENSE ? kWarps : 1;
+  // one record (total, overflow mark, spill region) per warp, each owning a
+  // contiguous range of chunks
+  const unsigned long long per_record = kWarps;
   unsigned long long records = std::min<unsigned long long>(
       p.num_chunks, static_cast<unsigned long long>(per_sm) * di.sm_count * per_record);
   p.chunks_per_cta = (p.num_chunks + records - 1) / records;
@@ -984,6 +1066,7 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   a.x_smem = p.x_smem;
   a.stages = p.stages;
   a.records = p.records;
+  a.spec = p.spec ? 1 : 0;
   a.emit_group = p.emit_group;
   // byte groups of h: the longest prefix whose weights 2^(s*k) fit in a byte
   const int s = f->s, q = f->q;

@@ -178,7 +178,9 @@ def test_async_entry_point_and_count():
     dict(spill_entries=1), dict(spill_entries=100), dict(lane_bytes=4, stages=2),
     dict(lane_bytes=37, stages=4), dict(lane_bytes=1000, stages=2, ctas_per_sm=1),
     dict(lane_bytes=260, spill_entries=5000), dict(mode=1, lane_bytes=68),
-    dict(mode=2), dict(mode=2, lane_bytes=3001, spill_entries=77), dict(mode=2, lane_bytes=8)])
+    dict(mode=2), dict(mode=2, lane_bytes=3001, spill_entries=77), dict(mode=2, lane_bytes=8),
+    dict(speculate=1), dict(speculate=1, mode=2), dict(speculate=-1),
+    dict(speculate=1, spill_entries=3), dict(speculate=1, lane_bytes=5, stages=4)])
 def test_launch_options_and_spill_overflow(opts):
     """Every launch shape gives the same positions, including spill regions
     too small for the occurrences (the emit kernel re-scans those chunks)."""
@@ -226,6 +228,38 @@ def test_dense_mode_m_equals_q(opts):
             assert int(cnt.item()) == want.size, (sigma, m, opts)
             k = min(cap, want.size)
             assert np.array_equal(pos[:k].cpu().numpy().view(np.uint64), want[:k]), (sigma, m, opts)
+        f.free()
+
+
+@pytest.mark.parametrize("speculate", [1, -1])
+def test_speculative_and_per_lane_forms(speculate):
+    """Both forms of the staged/direct scan against the oracle, for every q,
+    long patterns with full-window matches and periodic texts."""
+    hc = _hc()
+    rng = np.random.default_rng(500 + speculate)
+    for trial in range(40):
+        sigma = int(rng.choice([1, 2, 4, 20, 95]))
+        m = int(rng.choice([3, 5, 9, 16, 33, 100, 300, 1024]))
+        q = int(rng.integers(1, min(m, 8) + 1))
+        if q == m:
+            q = max(1, m - 1)
+        alpha = int(rng.choice([4, 8, 11, 12, 15]))
+        x, y = _case(rng, sigma, int(rng.integers(1000, 400_000)), m, plant=int(rng.integers(0, 30)))
+        want = oracle.hc_search(x, y, q, alpha)
+        y_dev, keep = _upload(y, offset=int(rng.integers(0, 16)))
+        f = hc.hc_preprocess(x, q, alpha)
+        for mode in (1, 2):
+            pos = torch.full((want.size + 4,), -1, dtype=torch.int64, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            try:
+                hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(mode=mode, speculate=speculate))
+            except hc.HCError as ex:      # staging buffers too large for this m, alpha
+                assert mode == 1 and ex.code == hc.HC_ERR_ARG
+                continue
+            torch.cuda.synchronize()
+            hc.hc_check_status()
+            assert int(cnt.item()) == want.size, (sigma, m, q, alpha, mode)
+            assert np.array_equal(pos[:want.size].cpu().numpy().view(np.uint64), want)
         f.free()
 
 
