@@ -104,3 +104,11 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 }
 
 }  // namespace hc
+
+namespace hc {
+// Invalidates an mbarrier whose phases are all complete, so that its memory
+// can be initialised again.
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+}  // namespace hc

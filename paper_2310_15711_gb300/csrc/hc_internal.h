@@ -105,6 +105,8 @@ struct SearchPlan {
 
 int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, int dev,
                 SearchPlan* out);
+// Device address of the library's status word on the current device.
+unsigned int* status_word();
 int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
                    uint64_t* pos, size_t cap, uint64_t* count_dev, void* ws,
                    cudaStream_t stream);
