@@ -58,6 +58,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", choices=["sweep", "batched"], default="sweep",
+                    help="sweep: the plain-HC sweep (default); batched: 4096 queries in one "
+                         "graph-captured batch vs. one plain launch per query")
+    ap.add_argument("--batch-queries", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -376,6 +380,107 @@ def run_gpu(args, rank, world, local_rank):
             f.free()
 
 
+def run_batched(args, rank, world, local_rank):
+    """The batched workload: hc_batch_queries(4096) -- n log-uniform 4 KiB to
+    64 MiB, m log-uniform 4 to 512, sigma from {4, 20}, each pattern copied
+    from its own text -- searched by one batch (device preprocessing, one
+    persistent scan over a work queue, emit) replayed as a CUDA graph, and by
+    one plain hc_search_async launch per query with host-built filters.
+    Reports text GB/s of both (sum of n over device time) and their ratio."""
+    import torch
+    import paper_2310_15711_gb300 as hc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    hc.build()
+    hc.lib()
+    qrs = hi.batch_queries(args.batch_queries, seed=4)
+    offs, total = [], 0
+    for qr in qrs:
+        offs.append(total)
+        total += (qr.n + 15) // 16 * 16
+    ybuf = torch.empty(total, dtype=torch.uint8, device=dev)
+    queries, host_x = [], []
+    caps = [int(2 * qr.n / float(qr.sigma) ** min(qr.m, 30)) + 64 for qr in qrs]
+    pos = torch.empty(sum(caps), dtype=torch.int64, device=dev)
+    counts = torch.zeros(len(qrs), dtype=torch.int64, device=dev)
+    counts_plain = torch.zeros(len(qrs), dtype=torch.int64, device=dev)
+    pos_plain = torch.empty(sum(caps), dtype=torch.int64, device=dev)
+    pofs = np.concatenate([[0], np.cumsum(caps)])
+    for i, qr in enumerate(qrs):
+        y = ybuf[offs[i]:offs[i] + qr.n]
+        y.copy_(hi.device_uniform_text(qr.n, qr.sigma, qr.text_seed, dev))
+        po = int(np.random.default_rng(qr.pattern_seed).integers(0, qr.n - qr.m + 1))
+        x = y[po:po + qr.m].clone()
+        host_x.append(x.cpu().numpy())
+        queries.append(dict(x_dev=x, y_dev=y, q=qr.q, alpha=qr.alpha,
+                            pos_dev=pos[pofs[i]:pofs[i + 1]], count_dev=counts[i:i + 1]))
+    text_bytes = float(sum(qr.n for qr in qrs))
+    stream = torch.cuda.Stream(device=dev)
+    b = hc.hc_batch_create(queries)
+    with torch.cuda.stream(stream):
+        b.run(stream=stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        b.run(stream=stream)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            g.replay()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        e1.record(stream)
+    stream.synchronize()
+    hc.hc_check_status(stream)
+    t_batch = e0.elapsed_time(e1) / args.steps / 1e3
+
+    filters = []
+    for i, qr in enumerate(qrs):
+        f = hc.hc_preprocess(host_x[i], qr.q, qr.alpha)
+        f.to_device()
+        filters.append(f)
+
+    def plain_pass():
+        for i, qr in enumerate(qrs):
+            hc.hc_search_async(filters[i], queries[i]["y_dev"], pos_plain[pofs[i]:pofs[i + 1]],
+                               counts_plain[i:i + 1], stream=stream)
+
+    with torch.cuda.stream(stream):
+        plain_pass()
+        stream.synchronize()
+        e2, e3 = ev(), ev()
+        e2.record(stream)
+        for _ in range(max(1, args.steps // 2)):
+            plain_pass()
+        e3.record(stream)
+    stream.synchronize()
+    t_plain = e2.elapsed_time(e3) / max(1, args.steps // 2) / 1e3
+    same = bool(torch.equal(counts, counts_plain))
+    line = {
+        "metric": "batched HC: text GB/s (device-timed, graph replay)",
+        "value": round(text_bytes / t_batch / GB, 2), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_batch * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "batched HC", "queries": len(qrs), "text_bytes": int(text_bytes),
+                   "n": "log-uniform 4 KiB .. 64 MiB", "m": "log-uniform 4 .. 512",
+                   "sigma": "{4, 20}", "q_alpha": "paper's choice per text type and m"},
+        "queries_per_s": round(len(qrs) / t_batch, 1),
+        "plain_launch_GBps": round(text_bytes / t_plain / GB, 2),
+        "plain_launch_ms": round(t_plain * 1e3, 3),
+        "speedup_vs_plain": round(t_plain / t_batch, 3),
+        "counts_equal_plain": same,
+        "batch_info": b.info(),
+    }
+    print(json.dumps(line), flush=True)
+    b.destroy()
+    for f in filters:
+        f.free()
+
+
 def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream):
     """One sweep step through hc_search (the synchronous C-ABI call): per
     sigma the text is copied from pinned host memory to the device, every
@@ -419,6 +524,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batched":
+        run_batched(args, rank, world, local_rank)
         return
     if world > 1:
         import torch

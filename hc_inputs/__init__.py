@@ -229,6 +229,18 @@ def batch_queries(count: int = 4096, seed: int = 4, n_lo: int = 4 << 10,
     return out
 
 
+def device_uniform_text(n: int, sigma: int, seed: int, device):
+    """n bytes i.i.d. uniform over the sigma-symbol alphabet, drawn on a CUDA
+    device with torch's seeded generator (for workloads too large to draw on
+    the host; the same seed and device type give the same bytes)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    idx = torch.randint(0, sigma, (n,), generator=g, device=device, dtype=torch.int64)
+    lut = torch.from_numpy(alphabet(sigma).copy()).to(device)
+    return lut[idx]
+
+
 def query_inputs(qr: Query):
     """(x, y) of one workload query."""
     y = uniform_text(qr.n, qr.sigma, qr.text_seed)

@@ -102,7 +102,8 @@ int hc_filter_to_device(hc_filter *f);
  * hc_search_async: y_dev is the text (n bytes, device memory, any alignment);
  * pos_dev receives the first min(count, cap) occurrence positions in
  * ascending order (may be NULL when cap = 0); count_dev (device memory, one
- * uint64) receives the total count.  Nothing is waited for.  The first call
+ * uint64) receives the total count.  Both must be 8-byte aligned (any
+ * element of a uint64 array is), else HC_ERR_ARG.  Nothing is waited for.  The first call
  * with a filter copies it to the device (see hc_filter_to_device).  Each call
  * takes a stream-ordered workspace from the library's memory pool and gives
  * it back after its kernels: 16 bytes per CTA plus 4 bytes per spilled
@@ -168,6 +169,63 @@ int hc_search_ex(const hc_filter *f, const uint8_t *y_dev, size_t n,
 int hc_search(const hc_filter *f, const uint8_t *x, const uint8_t *y_dev,
               size_t n, uint64_t *pos_dev, size_t cap, size_t *count,
               hc_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batched search: many (pattern, text) queries in one set of launches.
+ *
+ * Each query is a search of hc_search_async (same results) with the pattern
+ * already in device memory.  hc_batch_create checks and plans the table
+ * once: it allocates the filters, the launch tables and the workspace on the
+ * current device (cudaMalloc) and keeps the query table's pointers, which
+ * must stay valid until hc_batch_destroy.  hc_batch_run then enqueues three
+ * kernels on `stream` and allocates nothing, so it may be captured in a CUDA
+ * graph and replayed: the preprocessing phase of every query on the device
+ * (Sec. 3.1, Eq. 1-5; F equals hc_preprocess's word for word), one
+ * persistent scan over a device-side work queue of (query, text range)
+ * tiles, and the output of positions and counts.  Runs on the same batch
+ * must not overlap on the GPU.  q and alpha are per query (for instance
+ * chosen by the autotuner); lane_bytes and mode (HC_MODE_AUTO, _STAGED or
+ * _DIRECT; m = q runs in the staged form) are launch options, 0 =
+ * automatic.
+ */
+typedef struct hc_batch_query {
+    const uint8_t *x_dev;   /* pattern, m bytes, device memory */
+    uint64_t m;
+    const uint8_t *y_dev;   /* text, n bytes, device memory (any alignment) */
+    uint64_t n;
+    int q, alpha;           /* 1 <= q <= min(m, 8), 1 <= alpha <= 15 */
+    uint64_t *pos_dev;      /* first min(count, cap) positions, ascending;
+                               8-byte aligned, like count_dev */
+    uint64_t cap;
+    uint64_t *count_dev;    /* total occurrences (one uint64, device) */
+    int lane_bytes;         /* window starts per lane and chunk, 0 = auto */
+    int mode;               /* HC_MODE_AUTO, HC_MODE_STAGED or HC_MODE_DIRECT */
+} hc_batch_query;
+
+typedef struct hc_batch hc_batch;
+
+/* Errors: HC_ERR_ARG (null pointer or parameter out of range, with the query
+ * index in hc_last_error), HC_ERR_NOMEM, HC_ERR_CUDA. */
+int hc_batch_create(const hc_batch_query *queries, size_t nq, hc_batch **out);
+
+/* Enqueues one run of every query.  Errors: HC_ERR_ARG, HC_ERR_STATE (other
+ * device), HC_ERR_CUDA; a device wait that gave up is reported by
+ * hc_check_status. */
+int hc_batch_run(hc_batch *b, hc_stream_t stream);
+
+/* Plan figures: work tiles, per-warp records, workspace bytes (any pointer
+ * may be NULL).  Errors: HC_ERR_ARG. */
+int hc_batch_info(const hc_batch *b, uint64_t *tiles, uint64_t *records,
+                  uint64_t *workspace_bytes);
+
+/* After a run has completed: copies query `query`'s filter (2^alpha words,
+ * F must hold nwords >= 2^alpha) and H_v to host memory (either may be
+ * NULL).  Synchronous.  Errors: HC_ERR_ARG, HC_ERR_CUDA. */
+int hc_batch_filter(const hc_batch *b, size_t query, uint32_t *F, size_t nwords,
+                    uint32_t *hv);
+
+/* Frees a batch and its device memory.  NULL is a no-op. */
+void hc_batch_destroy(hc_batch *b);
 
 /* ------------------------------------------------------------------------
  * hc_search_noalloc: the search of hc_search_async for callers that cannot

@@ -64,6 +64,13 @@ SIGNATURES = {
     "hc_search": (ctypes.c_int, [_vp, _vp, _vp, _sz, _vp, _sz, ctypes.POINTER(_sz), _vp]),
     "hc_search_ex": (ctypes.c_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _vp]),
     "hc_search_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, _sz, _vp, _vp]),
+    "hc_batch_create": (ctypes.c_int, [_vp, _sz, ctypes.POINTER(_vp)]),
+    "hc_batch_run": (ctypes.c_int, [_vp, _vp]),
+    "hc_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_uint64),
+                                     ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "hc_batch_filter": (ctypes.c_int, [_vp, _sz, ctypes.POINTER(ctypes.c_uint32), _sz,
+                                       ctypes.POINTER(ctypes.c_uint32)]),
+    "hc_batch_destroy": (None, [_vp]),
     "hc_check_status": (ctypes.c_int, [_vp]),
     "hc_kernel_launches": (ctypes.c_uint64, []),
     "hc_timing_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -271,6 +278,81 @@ def hc_search_noalloc(f: HCFilter, F_dev, x_dev, y_dev, pos_dev, count_dev,
     _check(lib().hc_search_noalloc(f.handle, _dev_ptr(F_dev), _dev_ptr(x_dev), _dev_ptr(y_dev), n,
                                    _dev_ptr(pos_dev), int(cap), _dev_ptr(count_dev),
                                    _stream_handle(stream)), "hc_search_noalloc")
+
+
+class BatchQuery(ctypes.Structure):
+    """hc_batch_query."""
+    _fields_ = [("x_dev", _vp), ("m", ctypes.c_uint64), ("y_dev", _vp), ("n", ctypes.c_uint64),
+                ("q", ctypes.c_int), ("alpha", ctypes.c_int), ("pos_dev", _vp),
+                ("cap", ctypes.c_uint64), ("count_dev", _vp), ("lane_bytes", ctypes.c_int),
+                ("mode", ctypes.c_int)]
+
+
+class HCBatch:
+    """An hc_batch: a planned table of (pattern, text) queries.
+
+    queries: list of dicts with keys x_dev, y_dev (uint8 CUDA tensors), q,
+    alpha, pos_dev (int64 CUDA tensor or None), count_dev (int64 CUDA tensor
+    of one element) and optionally cap, lane_bytes, mode.  The tensors must
+    stay alive while the batch exists."""
+
+    def __init__(self, queries):
+        n = len(queries)
+        arr = (BatchQuery * max(n, 1))()
+        for i, d in enumerate(queries):
+            pos = d.get("pos_dev")
+            arr[i].x_dev = _dev_ptr(d["x_dev"])
+            arr[i].m = d["x_dev"].numel()
+            arr[i].y_dev = _dev_ptr(d["y_dev"])
+            arr[i].n = d["y_dev"].numel() if "n" not in d else int(d["n"])
+            arr[i].q = int(d["q"])
+            arr[i].alpha = int(d["alpha"])
+            arr[i].pos_dev = _dev_ptr(pos) if pos is not None else None
+            arr[i].cap = int(d.get("cap", pos.numel() if pos is not None else 0))
+            arr[i].count_dev = _dev_ptr(d["count_dev"])
+            arr[i].lane_bytes = int(d.get("lane_bytes", 0))
+            arr[i].mode = int(d.get("mode", 0))
+        self._keep = (arr, queries)
+        h = _vp()
+        _check(lib().hc_batch_create(ctypes.cast(arr, _vp), n, ctypes.byref(h)), "hc_batch_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("batch has been destroyed")
+        return self._h
+
+    def run(self, stream=None):
+        _check(lib().hc_batch_run(self.handle, _stream_handle(stream)), "hc_batch_run")
+
+    def info(self):
+        t, r, w = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().hc_batch_info(self.handle, ctypes.byref(t), ctypes.byref(r), ctypes.byref(w)),
+               "hc_batch_info")
+        return {"tiles": t.value, "records": r.value, "workspace_bytes": w.value}
+
+    def filter(self, i: int, alpha: int):
+        F = np.zeros(1 << alpha, dtype=np.uint32)
+        hv = ctypes.c_uint32()
+        _check(lib().hc_batch_filter(self.handle, i, F.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                     F.size, ctypes.byref(hv)), "hc_batch_filter")
+        return F, hv.value
+
+    def destroy(self):
+        if self._h is not None and _lib is not None:
+            _lib.hc_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def hc_batch_create(queries) -> HCBatch:
+    return HCBatch(queries)
 
 
 def hc_check_status(stream=None) -> None:

@@ -41,6 +41,9 @@ inline Filter* as_filter(const hc_filter* f) {
   return (p != nullptr && p->magic == kFilterMagic) ? p : nullptr;
 }
 
+// uint64 outputs (positions, counts) need their natural alignment; NULL passes.
+inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0u; }
+
 // Error reporting: per-thread last message.
 int set_error(int code, const std::string& msg);
 int cuda_error(cudaError_t e, const char* where);

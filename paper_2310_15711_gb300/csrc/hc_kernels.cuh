@@ -32,7 +32,7 @@ struct SearchArgs {
   const uint32_t* F;         // filter words (device), fwords of them
   const uint8_t* x;          // pattern (device)
   uint32_t fwords;
-  int m, s;
+  int m, q, s;
   uint32_t mask, hv;
   unsigned long long* pos;   // output positions (device), cap of them
   unsigned long long cap;
@@ -549,7 +549,9 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
     const uint4* r4 = reinterpret_cast<const uint4*>(region);
     const unsigned long long nvec = (ncopy + 3) / 4;
     const unsigned long long stride = static_cast<unsigned long long>(kThreads) * kEmitSplit;
-    const bool even = (P & 1ull) == 0ull;
+    // 16-byte stores only where the output address itself is 16-byte aligned
+    // (k is a multiple of 4, so a.pos + P + k is aligned iff a.pos + P is)
+    const bool even = (reinterpret_cast<uintptr_t>(a.pos + P) & 15u) == 0u;
     for (unsigned long long k0 = part * kThreads + tid; k0 < nvec; k0 += 4 * stride) {
       uint4 v[4];
 #pragma unroll

@@ -65,7 +65,8 @@ extern "C" int hc_search_noalloc(const hc_filter* fp, const uint32_t* F_dev, con
   if (f == nullptr) return set_error(HC_ERR_ARG, "hc_search_noalloc: invalid filter");
   if (F_dev == nullptr || x_dev == nullptr)
     return set_error(HC_ERR_ARG, "hc_search_noalloc: F_dev and x_dev are required");
-  if (count_dev == nullptr) return set_error(HC_ERR_ARG, "hc_search_noalloc: count_dev is NULL");
+  if (count_dev == nullptr || !aligned8(count_dev) || !aligned8(pos_dev))
+    return set_error(HC_ERR_ARG, "hc_search_noalloc: count_dev NULL, or pos/count not 8-byte aligned");
   if (y_dev == nullptr && n > 0) return set_error(HC_ERR_ARG, "hc_search_noalloc: y_dev is NULL");
   if (pos_dev == nullptr && cap > 0)
     return set_error(HC_ERR_ARG, "hc_search_noalloc: pos_dev is NULL with cap > 0");

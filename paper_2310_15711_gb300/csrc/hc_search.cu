@@ -496,6 +496,7 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   a.x = f->dev_x();
   a.fwords = static_cast<uint32_t>(f->F.size());
   a.m = static_cast<int>(f->m);
+  a.q = f->q;
   a.s = f->s;
   a.mask = f->mask;
   a.hv = f->hv;
@@ -626,6 +627,7 @@ int check_search_args(const char* who, Filter* f, const uint8_t* y_dev, size_t n
   if (y_dev == nullptr && n > 0) return set_error(HC_ERR_ARG, std::string(who) + ": y_dev is NULL");
   if (pos_dev == nullptr && cap > 0)
     return set_error(HC_ERR_ARG, std::string(who) + ": pos_dev is NULL with cap > 0");
+  if (!aligned8(pos_dev)) return set_error(HC_ERR_ARG, std::string(who) + ": pos_dev not 8-byte aligned");
   return HC_OK;
 }
 }  // namespace
@@ -639,7 +641,8 @@ int hc_search_ex(const hc_filter* fp, const uint8_t* y_dev, size_t n, uint64_t* 
   Filter* f = as_filter(fp);
   int rc = check_search_args("hc_search_ex", f, y_dev, n, pos_dev, cap);
   if (rc != HC_OK) return rc;
-  if (count_dev == nullptr) return set_error(HC_ERR_ARG, "hc_search_ex: count_dev is NULL");
+  if (count_dev == nullptr || !aligned8(count_dev))
+    return set_error(HC_ERR_ARG, "hc_search_ex: count_dev is NULL or not 8-byte aligned");
   if (opts != nullptr && opts->struct_size != sizeof(hc_search_opts))
     return set_error(HC_ERR_ARG, "hc_search_ex: opts->struct_size mismatch");
   return launch_search(f, y_dev, n, pos_dev, cap, count_dev, opts,
@@ -652,7 +655,8 @@ int hc_search_async(const hc_filter* fp, const uint8_t* y_dev, size_t n, uint64_
   Filter* f = as_filter(fp);
   int rc = check_search_args("hc_search_async", f, y_dev, n, pos_dev, cap);
   if (rc != HC_OK) return rc;
-  if (count_dev == nullptr) return set_error(HC_ERR_ARG, "hc_search_async: count_dev is NULL");
+  if (count_dev == nullptr || !aligned8(count_dev))
+    return set_error(HC_ERR_ARG, "hc_search_async: count_dev is NULL or not 8-byte aligned");
   return launch_search(f, y_dev, n, pos_dev, cap, count_dev, nullptr,
                        reinterpret_cast<cudaStream_t>(stream));
 }

@@ -263,6 +263,52 @@ def test_speculative_and_per_lane_forms(speculate):
         f.free()
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_positions_at_8_byte_aligned_offset(mode):
+    """Output buffers that are slices of a larger int64 buffer start on an
+    8-byte (not 16-byte) boundary: every kernel kind writes the same
+    positions there, and nothing before or after the slice is touched."""
+    hc = _hc()
+    rng = np.random.default_rng(61 + mode)
+    m = 4 if mode == 3 else 6
+    q = 4 if mode == 3 else 3
+    x, y = _case(rng, 2, 900_001, m, plant=30)
+    want = oracle.hc_search(x, y, q, 12)
+    assert want.size > 10_000
+    y_dev, keep = _upload(y, offset=3)
+    f = hc.hc_preprocess(x, q, 12)
+    for lead in (1, 2, 3):
+        big = torch.full((want.size + 8,), -7, dtype=torch.int64, device="cuda")
+        cnt_big = torch.full((3,), -7, dtype=torch.int64, device="cuda")
+        pos, cnt = big[lead:lead + want.size + 1], cnt_big[1:2]
+        hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(mode=mode))
+        torch.cuda.synchronize()
+        hc.hc_check_status()
+        assert int(cnt.item()) == want.size
+        got = big.cpu().numpy()
+        assert np.array_equal(got[lead:lead + want.size].view(np.uint64), want), lead
+        assert (got[:lead] == -7).all() and (got[lead + want.size:] == -7).all()
+        assert cnt_big[0].item() == -7 and cnt_big[2].item() == -7
+    f.free()
+
+
+def test_misaligned_output_pointers_rejected():
+    """A positions or count pointer that is not 8-byte aligned is an argument
+    error, reported before anything is launched."""
+    hc = _hc()
+    y_dev, keep = _upload(np.frombuffer(b"ACGT" * 1000, np.uint8))
+    f = hc.hc_preprocess(b"ACGTACGT", 4, 12)
+    raw = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for pos, c in ((raw[4:132], cnt), (None, raw[4:12]), (raw[1:129], cnt)):
+        with pytest.raises(hc.HCError) as ei:
+            hc.hc_search_async(f, y_dev, pos, c, cap=16 if pos is not None else 0)
+        assert ei.value.code == hc.HC_ERR_ARG
+    torch.cuda.synchronize()
+    assert (raw == 0).all()
+    f.free()
+
+
 def test_search_opts_rejected_when_out_of_range():
     hc = _hc()
     y_dev, keep = _upload(np.frombuffer(b"ACGT" * 1000, np.uint8))
