@@ -62,6 +62,8 @@ def parse_args():
                     help="sweep: the plain-HC sweep (default); batched: 4096 queries in one "
                          "graph-captured batch vs. one plain launch per query")
     ap.add_argument("--batch-queries", type=int, default=4096)
+    ap.add_argument("--tune-text-bytes", type=int, default=256 << 20,
+                    help="calibration text per alphabet size (batched workload)")
     return ap.parse_args()
 
 
@@ -380,13 +382,19 @@ def run_gpu(args, rank, world, local_rank):
             f.free()
 
 
+BATCH_TUNE_MS = (4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512)
+
+
 def run_batched(args, rank, world, local_rank):
-    """The batched workload: hc_batch_queries(4096) -- n log-uniform 4 KiB to
+    """The batched workload: batch_queries(4096) -- n log-uniform 4 KiB to
     64 MiB, m log-uniform 4 to 512, sigma from {4, 20}, each pattern copied
-    from its own text -- searched by one batch (device preprocessing, one
-    persistent scan over a work queue, emit) replayed as a CUDA graph, and by
-    one plain hc_search_async launch per query with host-built filters.
-    Reports text GB/s of both (sum of n over device time) and their ratio."""
+    from its own text.  The autotuner is calibrated first (sigma in {4, 20},
+    m on a log grid from 4 to 512, 256 MiB calibration texts; untimed), then
+    one batch with every query's parameters from the tuner (alphabet size
+    measured from each text on the device) runs as a CUDA graph replay.
+    Compared with the same batch on the paper's (q, alpha) and with one plain
+    hc_search_async launch per query (host-built filters, tuned q, alpha).
+    Reports text GB/s (sum of n over device time) of each and the ratios."""
     import torch
     import paper_2310_15711_gb300 as hc
 
@@ -400,53 +408,76 @@ def run_batched(args, rank, world, local_rank):
         offs.append(total)
         total += (qr.n + 15) // 16 * 16
     ybuf = torch.empty(total, dtype=torch.uint8, device=dev)
-    queries, host_x = [], []
+    host_x = []
     caps = [int(2 * qr.n / float(qr.sigma) ** min(qr.m, 30)) + 64 for qr in qrs]
-    pos = torch.empty(sum(caps), dtype=torch.int64, device=dev)
-    counts = torch.zeros(len(qrs), dtype=torch.int64, device=dev)
-    counts_plain = torch.zeros(len(qrs), dtype=torch.int64, device=dev)
-    pos_plain = torch.empty(sum(caps), dtype=torch.int64, device=dev)
     pofs = np.concatenate([[0], np.cumsum(caps)])
+    pos = {k: torch.empty(int(pofs[-1]), dtype=torch.int64, device=dev) for k in ("tuned", "paper", "plain")}
+    counts = {k: torch.zeros(len(qrs), dtype=torch.int64, device=dev) for k in ("tuned", "paper", "plain")}
+    xs = []
     for i, qr in enumerate(qrs):
         y = ybuf[offs[i]:offs[i] + qr.n]
         y.copy_(hi.device_uniform_text(qr.n, qr.sigma, qr.text_seed, dev))
         po = int(np.random.default_rng(qr.pattern_seed).integers(0, qr.n - qr.m + 1))
-        x = y[po:po + qr.m].clone()
-        host_x.append(x.cpu().numpy())
-        queries.append(dict(x_dev=x, y_dev=y, q=qr.q, alpha=qr.alpha,
-                            pos_dev=pos[pofs[i]:pofs[i + 1]], count_dev=counts[i:i + 1]))
+        xs.append(y[po:po + qr.m].clone())
+        host_x.append(xs[-1].cpu().numpy())
     text_bytes = float(sum(qr.n for qr in qrs))
     stream = torch.cuda.Stream(device=dev)
-    b = hc.hc_batch_create(queries)
+
+    def queries(kind):
+        out = []
+        for i, qr in enumerate(qrs):
+            d = dict(x_dev=xs[i], y_dev=ybuf[offs[i]:offs[i] + qr.n],
+                     pos_dev=pos[kind][pofs[i]:pofs[i + 1]], count_dev=counts[kind][i:i + 1])
+            if kind == "paper":
+                d.update(q=qr.q, alpha=qr.alpha)
+            else:
+                d.update(q=0, sigma=0)       # tuned; alphabet size measured from the text
+            out.append(d)
+        return out
+
+    tuner = hc.HCTuner()
+    t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        b.run(stream=stream)
-    stream.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=stream):
-        b.run(stream=stream)
+        tuner.calibrate([4, 20], BATCH_TUNE_MS, text_bytes=args.tune_text_bytes, seed=11, stream=stream)
+    tune_s = time.perf_counter() - t0
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            g.replay()
-        e0, e1 = ev(), ev()
-        e0.record(stream)
-        for _ in range(args.steps):
-            g.replay()
-        e1.record(stream)
-    stream.synchronize()
-    hc.hc_check_status(stream)
-    t_batch = e0.elapsed_time(e1) / args.steps / 1e3
+
+    def time_batch(b):
+        with torch.cuda.stream(stream):
+            b.run(stream=stream)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            b.run(stream=stream)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                g.replay()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(args.steps):
+                g.replay()
+            e1.record(stream)
+        stream.synchronize()
+        hc.hc_check_status(stream)
+        return e0.elapsed_time(e1) / args.steps / 1e3
+
+    launches0 = hc.hc_kernel_launches()
+    bt = hc.hc_batch_create_tuned(queries("tuned"), tuner)
+    t_batch = time_batch(bt)
+    tuned_params = [bt.params(i) for i in range(len(qrs))]
+    bp = hc.hc_batch_create(queries("paper"))
+    t_paper = time_batch(bp)
 
     filters = []
     for i, qr in enumerate(qrs):
-        f = hc.hc_preprocess(host_x[i], qr.q, qr.alpha)
+        f = hc.hc_preprocess(host_x[i], tuned_params[i]["q"], tuned_params[i]["alpha"])
         f.to_device()
         filters.append(f)
 
     def plain_pass():
         for i, qr in enumerate(qrs):
-            hc.hc_search_async(filters[i], queries[i]["y_dev"], pos_plain[pofs[i]:pofs[i + 1]],
-                               counts_plain[i:i + 1], stream=stream)
+            hc.hc_search_async(filters[i], ybuf[offs[i]:offs[i] + qr.n], pos["plain"][pofs[i]:pofs[i + 1]],
+                               counts["plain"][i:i + 1], stream=stream)
 
     with torch.cuda.stream(stream):
         plain_pass()
@@ -457,8 +488,11 @@ def run_batched(args, rank, world, local_rank):
             plain_pass()
         e3.record(stream)
     stream.synchronize()
+    hc.hc_check_status(stream)
     t_plain = e2.elapsed_time(e3) / max(1, args.steps // 2) / 1e3
-    same = bool(torch.equal(counts, counts_plain))
+    same = bool(torch.equal(counts["tuned"], counts["plain"]) and torch.equal(counts["tuned"], counts["paper"]))
+    nq_changed = sum(1 for i, qr in enumerate(qrs)
+                     if (tuned_params[i]["q"], tuned_params[i]["alpha"]) != (qr.q, qr.alpha))
     line = {
         "metric": "batched HC: text GB/s (device-timed, graph replay)",
         "value": round(text_bytes / t_batch / GB, 2), "unit": UNIT, "n_gpus": 1,
@@ -467,16 +501,26 @@ def run_batched(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": "batched HC", "queries": len(qrs), "text_bytes": int(text_bytes),
                    "n": "log-uniform 4 KiB .. 64 MiB", "m": "log-uniform 4 .. 512",
-                   "sigma": "{4, 20}", "q_alpha": "paper's choice per text type and m"},
+                   "sigma": "{4, 20}", "q_alpha": "autotuned per (measured sigma, m)",
+                   "l2": "27 GB of texts, far larger than L2; no flush"},
         "queries_per_s": round(len(qrs) / t_batch, 1),
+        "paper_params_GBps": round(text_bytes / t_paper / GB, 2),
+        "tuned_vs_paper": round(t_paper / t_batch, 3),
+        "queries_retuned": nq_changed,
         "plain_launch_GBps": round(text_bytes / t_plain / GB, 2),
         "plain_launch_ms": round(t_plain * 1e3, 3),
         "speedup_vs_plain": round(t_plain / t_batch, 3),
-        "counts_equal_plain": same,
-        "batch_info": b.info(),
+        "counts_equal": same,
+        "tune_s": round(tune_s, 2),
+        "tuner": tuner.entries(),
+        "batch_info": bt.info(),
+        "gpu_launches_per_step": 3,
+        "library_launches_total": hc.hc_kernel_launches() - launches0,
     }
     print(json.dumps(line), flush=True)
-    b.destroy()
+    bt.destroy()
+    bp.destroy()
+    tuner.free()
     for f in filters:
         f.free()
 

@@ -183,10 +183,14 @@ int hc_search(const hc_filter *f, const uint8_t *x, const uint8_t *y_dev,
  * (Sec. 3.1, Eq. 1-5; F equals hc_preprocess's word for word), one
  * persistent scan over a device-side work queue of (query, text range)
  * tiles, and the output of positions and counts.  Runs on the same batch
- * must not overlap on the GPU.  q and alpha are per query (for instance
- * chosen by the autotuner); lane_bytes and mode (HC_MODE_AUTO, _STAGED or
- * _DIRECT; m = q runs in the staged form) are launch options, 0 =
- * automatic.
+ * must not overlap on the GPU.  q and alpha are per query; lane_bytes and
+ * mode (HC_MODE_AUTO, _STAGED or _DIRECT; m = q runs in the staged form) are
+ * launch options, 0 = automatic.  A query with q = 0 takes q, alpha and the
+ * launch options from the autotuner given to hc_batch_create_tuned (from the
+ * paper's Tables 1-3 without one) for its text's alphabet size: `sigma`, or
+ * when sigma = 0 the effective alphabet size 1 / sum(p_c^2) of the byte
+ * frequencies of a sample of the text, measured on the device at creation
+ * (a nonzero lane_bytes or mode of the query still applies).
  */
 typedef struct hc_batch_query {
     const uint8_t *x_dev;   /* pattern, m bytes, device memory */
@@ -200,13 +204,39 @@ typedef struct hc_batch_query {
     uint64_t *count_dev;    /* total occurrences (one uint64, device) */
     int lane_bytes;         /* window starts per lane and chunk, 0 = auto */
     int mode;               /* HC_MODE_AUTO, HC_MODE_STAGED or HC_MODE_DIRECT */
+    int sigma;              /* alphabet size for q = 0 (0 = measure the text) */
+    int reserved;           /* 0 */
 } hc_batch_query;
 
 typedef struct hc_batch hc_batch;
 
+/* Search parameters of one (alphabet size, pattern length) cell: filter
+ * parameters q and alpha, launch options lane_bytes and mode, and the text
+ * rate measured for them (GB/s; 0 when not measured). */
+typedef struct hc_tune_entry {
+    int sigma;
+    int q, alpha, lane_bytes, mode;
+    int reserved;
+    uint64_t m;
+    double gbps;
+} hc_tune_entry;
+
+typedef struct hc_tuner hc_tuner;
+
 /* Errors: HC_ERR_ARG (null pointer or parameter out of range, with the query
  * index in hc_last_error), HC_ERR_NOMEM, HC_ERR_CUDA. */
 int hc_batch_create(const hc_batch_query *queries, size_t nq, hc_batch **out);
+
+/* hc_batch_create, with the parameters of q = 0 queries from `tuner` (NULL:
+ * the paper's Tables 1-3).  Synchronous when some query has q = 0 and
+ * sigma = 0 (the alphabet sizes are measured first).  Errors as
+ * hc_batch_create. */
+int hc_batch_create_tuned(const hc_batch_query *queries, size_t nq,
+                          const hc_tuner *tuner, hc_batch **out);
+
+/* The parameters query `query` runs with (q, alpha, resolved lane_bytes and
+ * mode; sigma and gbps are 0).  Errors: HC_ERR_ARG. */
+int hc_batch_params(const hc_batch *b, size_t query, hc_tune_entry *out);
 
 /* Enqueues one run of every query.  Errors: HC_ERR_ARG, HC_ERR_STATE (other
  * device), HC_ERR_CUDA; a device wait that gave up is reported by
@@ -226,6 +256,162 @@ int hc_batch_filter(const hc_batch *b, size_t query, uint32_t *F, size_t nwords,
 
 /* Frees a batch and its device memory.  NULL is a no-op. */
 void hc_batch_destroy(hc_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Autotuner: a table of search parameters per (alphabet size, pattern
+ * length) cell, measured on this GPU.  The paper picks q and alpha per text
+ * and pattern length from its measurements (Sec. 4, Tables 1-3); the tuner
+ * measures the same choice, plus the window starts per lane and the scan
+ * mode, on the batched kernels here.
+ *
+ * hc_tuner_create: an empty table; lookups then give the paper's choice
+ *   (nearest of its three texts by alphabet size: <= 8 genome, <= 40
+ *   protein, else English; nearest m on a log scale; q clamped to m).
+ * hc_tuner_calibrate: for every sigma of `sigmas` a calibration text of
+ *   text_bytes bytes drawn i.i.d. uniform over sigma symbols on the device
+ *   (seeded), for every m of `ms` a pattern copied from it; each candidate
+ *   (q in [1, min(8, m)], alpha in [8, 13]; then, for the best pair,
+ *   lane_bytes halved and doubled and both scan modes) runs as a one-query
+ *   batch, best of 3 timed runs; the fastest fills the (sigma, m) cell,
+ *   replacing an older one.  Synchronous on `stream`; allocates and frees
+ *   device memory (text_bytes plus workspace).
+ * hc_tuner_lookup: the cell nearest to (sigma, m) on log scales, q clamped
+ *   to m (the paper's choice when the table is empty).
+ * hc_tuner_save / hc_tuner_load: the table as text, one cell per line
+ *   ("sigma m q alpha lane_bytes mode gbps"); load adds to the table.
+ * Errors: HC_ERR_ARG, HC_ERR_NOMEM, HC_ERR_CUDA; HC_ERR_STATE for an
+ * unreadable or malformed file. */
+int hc_tuner_create(hc_tuner **out);
+int hc_tuner_calibrate(hc_tuner *t, const int *sigmas, size_t nsigma,
+                       const uint64_t *ms, size_t nm, uint64_t text_bytes,
+                       uint64_t seed, hc_stream_t stream);
+int hc_tuner_lookup(const hc_tuner *t, double sigma, uint64_t m,
+                    hc_tune_entry *out);
+/* Number of cells, and cell i of the table (sorted by sigma, then m). */
+int hc_tuner_size(const hc_tuner *t, size_t *count);
+int hc_tuner_entry(const hc_tuner *t, size_t i, hc_tune_entry *out);
+int hc_tuner_save(const hc_tuner *t, const char *path);
+int hc_tuner_load(hc_tuner *t, const char *path);
+void hc_tuner_free(hc_tuner *t);
+
+/* ------------------------------------------------------------------------
+ * Served search: a request loop with continuous batching.
+ *
+ * A server keeps registered texts resident in device memory and runs
+ * requests (a host pattern against one resident text) submitted from any
+ * host thread.  Its worker thread takes queued requests in order into
+ * batches (the batched search above: device preprocessing, persistent scan,
+ * emit) and runs up to max_inflight batches at once, each on its own
+ * stream: requests that arrive while earlier batches are on the GPU are
+ * launched as soon as a stream and memory are free, and their work overlaps
+ * with the earlier batches' on the device.  A request's result is the same
+ * as that of hc_search on its pattern and text, alone or in any mix.
+ *
+ * Admission: resident texts plus the device bytes of every admitted request
+ * (filter, pattern, launch tables, scan workspace) stay within mem_limit
+ * (default 32 GiB).  A request that does not fit waits until completed
+ * batches release memory; one that can never fit completes with
+ * HC_ERR_ADMISSION.  Queue order is kept.  Results (counts, positions) are
+ * written by the kernels into pinned host memory mapped into the device, so
+ * no copy step follows a batch.
+ *
+ * plain = 1 runs each request as one plain search launch (host-built filter,
+ * the kernels of hc_search_async) instead: the comparison form.
+ */
+typedef struct hc_server hc_server;
+
+typedef struct hc_server_config {
+    size_t struct_size;     /* sizeof(hc_server_config) */
+    uint64_t mem_limit;     /* device bytes: texts + admitted requests; 0 = 32 GiB */
+    int max_inflight;       /* batches on the device at once, 1..16; 0 = 3 */
+    int max_batch;          /* requests per batch, 1..2^20; 0 = 1024 */
+    uint64_t default_cap;   /* positions kept per request when its cap is 0; 0 = 4096 */
+    int plain;              /* 1: one plain search launch per request */
+    int reserved;
+} hc_server_config;
+
+typedef struct hc_server_request {
+    uint32_t text;          /* id from hc_server_add_text */
+    int q, alpha;           /* q = 0: from the server's tuner for the text's sigma */
+    int lane_bytes, mode;   /* launch options, 0 = tuned / automatic */
+    const uint8_t *x;       /* pattern, host memory (copied at submission) */
+    uint64_t m;             /* 1 .. 65536 */
+    uint64_t cap;           /* positions kept; 0 = default_cap */
+} hc_server_request;
+
+typedef struct hc_server_result {
+    uint64_t id;
+    int status;             /* HC_OK; HC_ERR_CAPACITY: count > cap, the first cap
+                               positions kept; HC_ERR_ADMISSION; HC_ERR_TIMEOUT (a
+                               device wait gave up); HC_ERR_CUDA; HC_ERR_STATE
+                               (cancelled by hc_server_destroy) */
+    uint32_t text;
+    int q, alpha;           /* the parameters it ran with */
+    uint64_t count;         /* total occurrences */
+    uint64_t npos;          /* positions in pos (ascending) */
+    const uint64_t *pos;    /* host memory, valid until hc_server_release(id) */
+    uint64_t submit_ns;     /* steady clock: submitted (replay: scheduled arrival) */
+    uint64_t start_ns;      /* its batch launched */
+    uint64_t done_ns;       /* its batch seen complete, results copied */
+    uint64_t batch;         /* batch number, and requests in that batch */
+    uint64_t batch_size;
+} hc_server_result;
+
+typedef struct hc_server_stats {
+    uint64_t submitted, completed, batches, rejected, admission_waits;
+    uint64_t max_batch, pending, inflight_bytes, peak_inflight_bytes;
+    uint64_t text_bytes, mem_limit;
+} hc_server_stats;
+
+/* Creates a server on the current device with its worker thread.  cfg may
+ * be NULL (defaults); tuner may be NULL (the paper's tables) and must
+ * outlive the server.  Errors: HC_ERR_ARG, HC_ERR_NOMEM, HC_ERR_CUDA. */
+int hc_server_create(const hc_server_config *cfg, const hc_tuner *tuner,
+                     hc_server **out);
+
+/* Registers a text: on_device = 0 copies n bytes from host memory into
+ * device memory the server owns; 1 keeps the caller's device pointer (valid
+ * until hc_server_destroy).  sigma = 0: the effective alphabet size is
+ * measured on the device (see hc_batch_create_tuned).  Synchronous.
+ * Errors: HC_ERR_ARG, HC_ERR_ADMISSION (texts beyond mem_limit),
+ * HC_ERR_CUDA. */
+int hc_server_add_text(hc_server *s, const uint8_t *y, uint64_t n,
+                       int on_device, int sigma, uint32_t *text_id);
+/* Length and (given or measured) alphabet size of a registered text. */
+int hc_server_text_info(const hc_server *s, uint32_t text_id, uint64_t *n,
+                        double *sigma);
+
+/* Queues one request; *id identifies its result.  The pattern is copied.
+ * Errors: HC_ERR_ARG (unknown text, parameters out of range), HC_ERR_STATE
+ * (server stopped after a CUDA error), HC_ERR_NOMEM. */
+int hc_server_submit(hc_server *s, const hc_server_request *r, uint64_t *id);
+
+/* Load generation: validates all n requests, then submits request i at
+ * arrival_ns[i] (non-decreasing) after the call started, from the calling
+ * thread; its latency counts from that scheduled time.  Returns when all
+ * are submitted.  Errors as hc_server_submit. */
+int hc_server_replay(hc_server *s, const hc_server_request *r, size_t n,
+                     const uint64_t *arrival_ns, uint64_t *ids);
+
+/* Up to max completed results not yet polled, waiting up to wait_us
+ * microseconds for the first (0: no wait, < 0: no limit). */
+int hc_server_poll(hc_server *s, hc_server_result *out, size_t max,
+                   size_t *got, int64_t wait_us);
+
+/* Frees a polled result's positions.  Errors: HC_ERR_ARG (unknown id),
+ * HC_ERR_STATE (not yet polled). */
+int hc_server_release(hc_server *s, uint64_t id);
+
+/* Waits until no request is queued or running (timeout_ms < 0: no limit).
+ * Errors: HC_ERR_TIMEOUT; HC_ERR_CUDA when the server stopped on a CUDA
+ * error. */
+int hc_server_drain(hc_server *s, int64_t timeout_ms);
+
+int hc_server_get_stats(const hc_server *s, hc_server_stats *out);
+
+/* Stops the worker (queued requests are cancelled, running batches
+ * finish), frees everything.  NULL is a no-op. */
+void hc_server_destroy(hc_server *s);
 
 /* ------------------------------------------------------------------------
  * hc_search_noalloc: the search of hc_search_async for callers that cannot

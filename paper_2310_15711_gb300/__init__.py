@@ -71,6 +71,18 @@ SIGNATURES = {
     "hc_batch_filter": (ctypes.c_int, [_vp, _sz, ctypes.POINTER(ctypes.c_uint32), _sz,
                                        ctypes.POINTER(ctypes.c_uint32)]),
     "hc_batch_destroy": (None, [_vp]),
+    "hc_batch_create_tuned": (ctypes.c_int, [_vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "hc_batch_params": (ctypes.c_int, [_vp, _sz, _vp]),
+    "hc_tuner_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
+    "hc_tuner_calibrate": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), _sz,
+                                          ctypes.POINTER(ctypes.c_uint64), _sz, ctypes.c_uint64,
+                                          ctypes.c_uint64, _vp]),
+    "hc_tuner_lookup": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _vp]),
+    "hc_tuner_size": (ctypes.c_int, [_vp, ctypes.POINTER(_sz)]),
+    "hc_tuner_entry": (ctypes.c_int, [_vp, _sz, _vp]),
+    "hc_tuner_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "hc_tuner_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "hc_tuner_free": (None, [_vp]),
     "hc_check_status": (ctypes.c_int, [_vp]),
     "hc_kernel_launches": (ctypes.c_uint64, []),
     "hc_timing_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -285,7 +297,77 @@ class BatchQuery(ctypes.Structure):
     _fields_ = [("x_dev", _vp), ("m", ctypes.c_uint64), ("y_dev", _vp), ("n", ctypes.c_uint64),
                 ("q", ctypes.c_int), ("alpha", ctypes.c_int), ("pos_dev", _vp),
                 ("cap", ctypes.c_uint64), ("count_dev", _vp), ("lane_bytes", ctypes.c_int),
-                ("mode", ctypes.c_int)]
+                ("mode", ctypes.c_int), ("sigma", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class TuneEntry(ctypes.Structure):
+    """hc_tune_entry."""
+    _fields_ = [("sigma", ctypes.c_int), ("q", ctypes.c_int), ("alpha", ctypes.c_int),
+                ("lane_bytes", ctypes.c_int), ("mode", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("m", ctypes.c_uint64), ("gbps", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k in ("sigma", "m", "q", "alpha", "lane_bytes", "mode", "gbps")}
+
+
+class HCTuner:
+    """An hc_tuner: search parameters per (alphabet size, pattern length)
+    cell, measured on this GPU by calibrate(); lookups on an empty table give
+    the paper's (q, alpha)."""
+
+    def __init__(self):
+        h = _vp()
+        _check(lib().hc_tuner_create(ctypes.byref(h)), "hc_tuner_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("tuner has been freed")
+        return self._h
+
+    def calibrate(self, sigmas, ms, text_bytes=256 << 20, seed=1, stream=None):
+        sa = (ctypes.c_int * len(sigmas))(*[int(v) for v in sigmas])
+        ma = (ctypes.c_uint64 * len(ms))(*[int(v) for v in ms])
+        _check(lib().hc_tuner_calibrate(self.handle, sa, len(sigmas), ma, len(ms), int(text_bytes),
+                                        int(seed), _stream_handle(stream)), "hc_tuner_calibrate")
+
+    def lookup(self, sigma: float, m: int) -> dict:
+        e = TuneEntry()
+        _check(lib().hc_tuner_lookup(self.handle, float(sigma), int(m), ctypes.byref(e)),
+               "hc_tuner_lookup")
+        return e.as_dict()
+
+    def entries(self) -> list:
+        n = _sz()
+        _check(lib().hc_tuner_size(self.handle, ctypes.byref(n)), "hc_tuner_size")
+        out = []
+        for i in range(n.value):
+            e = TuneEntry()
+            _check(lib().hc_tuner_entry(self.handle, i, ctypes.byref(e)), "hc_tuner_entry")
+            out.append(e.as_dict())
+        return out
+
+    def save(self, path: str):
+        _check(lib().hc_tuner_save(self.handle, os.fsencode(path)), "hc_tuner_save")
+
+    def load(self, path: str):
+        _check(lib().hc_tuner_load(self.handle, os.fsencode(path)), "hc_tuner_load")
+
+    def free(self):
+        if self._h is not None and _lib is not None:
+            _lib.hc_tuner_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hc_tuner_create() -> HCTuner:
+    return HCTuner()
 
 
 class HCBatch:
@@ -293,10 +375,11 @@ class HCBatch:
 
     queries: list of dicts with keys x_dev, y_dev (uint8 CUDA tensors), q,
     alpha, pos_dev (int64 CUDA tensor or None), count_dev (int64 CUDA tensor
-    of one element) and optionally cap, lane_bytes, mode.  The tensors must
-    stay alive while the batch exists."""
+    of one element) and optionally cap, lane_bytes, mode, sigma.  q = 0 (or
+    absent) takes the parameters from ``tuner`` (the paper's tables without
+    one).  The tensors must stay alive while the batch exists."""
 
-    def __init__(self, queries):
+    def __init__(self, queries, tuner: HCTuner | None = None):
         n = len(queries)
         arr = (BatchQuery * max(n, 1))()
         for i, d in enumerate(queries):
@@ -305,8 +388,9 @@ class HCBatch:
             arr[i].m = d["x_dev"].numel()
             arr[i].y_dev = _dev_ptr(d["y_dev"])
             arr[i].n = d["y_dev"].numel() if "n" not in d else int(d["n"])
-            arr[i].q = int(d["q"])
-            arr[i].alpha = int(d["alpha"])
+            arr[i].q = int(d.get("q", 0))
+            arr[i].alpha = int(d.get("alpha", 0))
+            arr[i].sigma = int(d.get("sigma", 0))
             arr[i].pos_dev = _dev_ptr(pos) if pos is not None else None
             arr[i].cap = int(d.get("cap", pos.numel() if pos is not None else 0))
             arr[i].count_dev = _dev_ptr(d["count_dev"])
@@ -314,8 +398,13 @@ class HCBatch:
             arr[i].mode = int(d.get("mode", 0))
         self._keep = (arr, queries)
         h = _vp()
-        _check(lib().hc_batch_create(ctypes.cast(arr, _vp), n, ctypes.byref(h)), "hc_batch_create")
+        if tuner is None:
+            _check(lib().hc_batch_create(ctypes.cast(arr, _vp), n, ctypes.byref(h)), "hc_batch_create")
+        else:
+            _check(lib().hc_batch_create_tuned(ctypes.cast(arr, _vp), n, tuner.handle, ctypes.byref(h)),
+                   "hc_batch_create_tuned")
         self._h = h
+        self._tuner = tuner
 
     @property
     def handle(self):
@@ -331,6 +420,13 @@ class HCBatch:
         _check(lib().hc_batch_info(self.handle, ctypes.byref(t), ctypes.byref(r), ctypes.byref(w)),
                "hc_batch_info")
         return {"tiles": t.value, "records": r.value, "workspace_bytes": w.value}
+
+    def params(self, i: int) -> dict:
+        """The (q, alpha, lane_bytes, mode) query i runs with."""
+        e = TuneEntry()
+        _check(lib().hc_batch_params(self.handle, i, ctypes.byref(e)), "hc_batch_params")
+        d = e.as_dict()
+        return {k: d[k] for k in ("q", "alpha", "lane_bytes", "mode")}
 
     def filter(self, i: int, alpha: int):
         F = np.zeros(1 << alpha, dtype=np.uint32)
@@ -353,6 +449,11 @@ class HCBatch:
 
 def hc_batch_create(queries) -> HCBatch:
     return HCBatch(queries)
+
+
+def hc_batch_create_tuned(queries, tuner: HCTuner | None) -> HCBatch:
+    """hc_batch_create_tuned; tuner None uses the paper's tables for q = 0."""
+    return HCBatch(queries, tuner)
 
 
 def hc_check_status(stream=None) -> None:

@@ -1,7 +1,7 @@
 // hc_batch.cu -- many (pattern, text) searches in one set of launches.
 //
-// hc_batch_create plans a table of queries once (and allocates everything
-// the runs need); hc_batch_run then enqueues three kernels and allocates
+// A batch is planned once on the host (launch arguments, work tables, sizes
+// of the filter and workspace areas) and run as three kernels that allocate
 // nothing, so a run can be captured in a CUDA graph and replayed:
 //
 //   1. hc_batch_preprocess_kernel -- the preprocessing phase of Sec. 3.1 on
@@ -18,30 +18,25 @@
 //      run the per-warp HC stream of the single search on one record each.
 //   3. hc_batch_emit_kernel -- per (query, record group): output offsets,
 //      copy of the spilled positions, re-scan of overflowed chunks, count.
+//
+// hc_batch_* (this file) owns a planned table in cudaMalloc'd memory; the
+// autotuner and the server build plans of their own with the same functions.
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
-#include "hc_kernels.cuh"
+#include "hc_batch_internal.h"
 
 namespace hc {
 namespace {
 
 constexpr uint32_t kBatchMagic = 0x48434231u;  // "HCB1"
 constexpr unsigned long long kTileTextBytes = 64ull << 10;  // text per record, about
-
-struct BatchTile {
-  uint32_t query;
-  uint32_t first_record;
-};
-
-struct EmitTile {
-  uint32_t query;
-  uint32_t group;
-};
 
 // h(x[i .. i+q-1]) by Horner's rule from the last byte down (Eq. 3, Eq. 4).
 __device__ __forceinline__ uint32_t pattern_hash(const uint8_t* x, int i, int q, int s,
@@ -108,11 +103,6 @@ __device__ __forceinline__ void stream_q(const SearchArgs& a, unsigned long long
   }
 }
 
-struct BatchLayout {
-  uint32_t f_bytes;        // shared memory for F (largest query)
-  uint32_t x_bytes;        // shared memory for x (largest staged pattern)
-  uint32_t ring_bytes;     // per-warp staging ring (largest query)
-};
 
 __global__ void __launch_bounds__(kThreads)
     hc_batch_scan_kernel(const SearchArgs* args, const BatchTile* tiles,
@@ -169,6 +159,34 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Byte histogram of a sample of each text (estimate_sigma).
+struct SigmaJob {
+  const uint8_t* y;
+  unsigned long long n;
+};
+
+constexpr unsigned long long kSigmaWhole = 64ull << 10;  // texts up to this: every byte
+constexpr unsigned long long kSigmaPiece = 4ull << 10;
+constexpr int kSigmaPieces = 16;
+
+__global__ void __launch_bounds__(kThreads) hc_sigma_kernel(const SigmaJob* jobs, uint32_t* hist) {
+  __shared__ uint32_t h[256];
+  const int tid = threadIdx.x;
+  h[tid] = 0;
+  __syncthreads();
+  const SigmaJob j = jobs[blockIdx.x];
+  if (j.n <= kSigmaWhole) {
+    for (unsigned long long i = tid; i < j.n; i += kThreads) atomicAdd(&h[j.y[i]], 1u);
+  } else {
+    for (int p = 0; p < kSigmaPieces; ++p) {
+      const unsigned long long start = (j.n - kSigmaPiece) * p / (kSigmaPieces - 1);
+      for (unsigned long long i = tid; i < kSigmaPiece; i += kThreads) atomicAdd(&h[j.y[start + i]], 1u);
+    }
+  }
+  __syncthreads();
+  hist[static_cast<size_t>(blockIdx.x) * 256 + tid] = h[tid];
+}
+
 template <typename T>
 int dev_alloc(T** p, size_t count, const char* what) {
   void* v = nullptr;
@@ -178,24 +196,240 @@ int dev_alloc(T** p, size_t count, const char* what) {
   return HC_OK;
 }
 
+// The batch kernels may use up to the device's opt-in shared memory; the
+// attribute is raised once per device, each launch asks for what it needs.
+int init_batch_kernels(int dev) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return HC_OK;
+  const DeviceInfo& di = device_info(dev);
+  const void* fns[3] = {reinterpret_cast<const void*>(hc_batch_preprocess_kernel),
+                        reinterpret_cast<const void*>(hc_batch_scan_kernel),
+                        reinterpret_cast<const void*>(hc_batch_emit_kernel)};
+  for (const void* fn : fns) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncGetAttributes(batch)");
+    const int dyn = static_cast<int>(di.smem_optin) - static_cast<int>(fa.sharedSizeBytes);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(batch)");
+  }
+  done.push_back(dev);
+  return HC_OK;
+}
+
 }  // namespace
+
+int plan_add_query(BatchPlan& plan, const hc_batch_query& Q, size_t i, const QueryParams& p,
+                   const char* who) {
+  char msg[200];
+  if (Q.x_dev == nullptr || Q.count_dev == nullptr || (Q.y_dev == nullptr && Q.n > 0) ||
+      (Q.pos_dev == nullptr && Q.cap > 0) || !aligned8(Q.pos_dev) || !aligned8(Q.count_dev)) {
+    std::snprintf(msg, sizeof msg, "%s: query %zu: null or misaligned pointer", who, i);
+    return set_error(HC_ERR_ARG, msg);
+  }
+  if (Q.m < 1 || p.q < 1 || p.q > kMaxQ || static_cast<uint64_t>(p.q) > Q.m || p.alpha < 1 ||
+      p.alpha > kMaxAlpha || Q.m > (uint64_t(1) << 30) || p.lane_bytes < 0 || p.lane_bytes > 4096 ||
+      (p.mode != HC_MODE_AUTO && p.mode != HC_MODE_STAGED && p.mode != HC_MODE_DIRECT)) {
+    std::snprintf(msg, sizeof msg,
+                  "%s: query %zu: need m >= 1, 1 <= q <= min(m, 8), 1 <= alpha <= 15, "
+                  "lane_bytes <= 4096, mode AUTO/STAGED/DIRECT", who, i);
+    return set_error(HC_ERR_ARG, msg);
+  }
+  const uint32_t qi = static_cast<uint32_t>(plan.args.size());
+  plan.args.emplace_back();
+  plan.params.push_back(p);
+  SearchArgs& a = plan.args.back();
+  a = SearchArgs{};
+  a.status = status_word();
+  a.y = Q.y_dev;
+  a.n = Q.n;
+  a.x = Q.x_dev;
+  a.m = static_cast<int>(Q.m);
+  a.q = p.q;
+  a.s = p.alpha / p.q;
+  a.fwords = 1u << p.alpha;
+  a.mask = a.fwords - 1u;
+  a.pos = reinterpret_cast<unsigned long long*>(Q.pos_dev);
+  a.cap = Q.pos_dev ? Q.cap : 0;
+  a.count_out = reinterpret_cast<unsigned long long*>(Q.count_dev);
+  {
+    int g = 1;
+    while (g < 4 && g < a.q && a.s * g <= 7) ++g;
+    a.g0 = g;
+    for (int k = 0; k < g; ++k) a.w0 |= (1u << (a.s * k)) << (8 * k);
+    for (int k = 0; k < a.q - g && k < 4; ++k) a.w1 |= (1u << (a.s * k)) << (8 * k);
+  }
+  plan.f_off.push_back(plan.filter_words);
+  plan.filter_words += (a.fwords + 3u) & ~3u;
+  plan.lay.f_bytes = std::max(plan.lay.f_bytes, a.fwords * 4u);
+  plan.ws_off.push_back(plan.ws_bytes);
+  if (Q.n < Q.m) {
+    a.records = 0;
+    return HC_OK;
+  }
+  const int shift = a.m - a.q + 1;
+  const bool direct = p.mode == HC_MODE_DIRECT ||
+                      (p.mode != HC_MODE_STAGED && (shift >= kDirectShift || Q.m > kMaxStagedM));
+  int L = p.lane_bytes;
+  if (L <= 0) L = direct ? std::min(4096, std::max(64, shift)) : 4 * std::min(std::max(16, shift) | 1, 47);
+  L = std::min(L, 4096);
+  a.L = L;
+  a.C = 32u * static_cast<uint32_t>(L);
+  a.stages = direct ? 0 : 2;
+  a.head = static_cast<int>(reinterpret_cast<uintptr_t>(Q.y_dev) & 15u);
+  a.stage_bytes = direct ? 0u : static_cast<uint32_t>(((16 + a.C + Q.m - 1 + 15) & ~uint64_t(15)) + 64);
+  a.x_smem = Q.m <= 4096 ? static_cast<uint32_t>((Q.m + 15) & ~uint64_t(15)) : 0u;
+  plan.lay.x_bytes = std::max(plan.lay.x_bytes, a.x_smem);
+  plan.lay.ring_bytes = std::max(plan.lay.ring_bytes, static_cast<uint32_t>(a.stages) * a.stage_bytes);
+  a.nwin = Q.n - Q.m + 1;
+  a.num_chunks = (a.nwin + a.C - 1) / a.C;
+  a.chunks_per_cta = std::max<unsigned long long>(1, (kTileTextBytes + a.C - 1) / a.C);
+  a.records = (a.num_chunks + a.chunks_per_cta - 1) / a.chunks_per_cta;
+  const unsigned long long spill =
+      a.cap == 0 ? 0 : std::min<unsigned long long>(a.nwin, std::max<unsigned long long>(a.cap, 4096));
+  a.region_entries = (std::max<unsigned long long>(1, (spill + a.records - 1) / a.records) + 3) & ~3ull;
+  plan.ws_bytes += a.records * 16 + a.records * a.region_entries * 4;
+  const unsigned long long groups = (a.records + 15) / 16;
+  a.emit_group = (a.records + groups - 1) / groups;
+  for (unsigned long long r = 0; r < a.records; r += kWarps)
+    plan.tiles.push_back({qi, static_cast<uint32_t>(r)});
+  for (unsigned long long g = 0; (g * a.emit_group) < a.records; ++g)
+    plan.etiles.push_back({qi, static_cast<uint32_t>(g)});
+  plan.records += a.records;
+  return HC_OK;
+}
+
+int plan_finish(BatchPlan& plan, int dev, const char* who) {
+  const DeviceInfo& di = device_info(dev);
+  plan.lay.f_bytes = (plan.lay.f_bytes + 15u) & ~15u;
+  plan.smem_pre = std::max<size_t>(plan.lay.f_bytes, 16);
+  plan.smem_scan = size_t(plan.lay.f_bytes) + plan.lay.x_bytes + size_t(kSlots) * kThreads * 4 +
+                   size_t(kWarps) * plan.lay.ring_bytes;
+  plan.smem_emit = size_t(plan.lay.f_bytes) + size_t(kSlots) * kThreads * 4;
+  if (plan.smem_scan + 2048 > di.smem_optin)
+    return set_error(HC_ERR_ARG, std::string(who) + ": filter and staging buffers exceed shared memory");
+  return init_batch_kernels(dev);
+}
+
+void plan_bind(BatchPlan& plan, uint32_t* d_filters, uint8_t* d_ws) {
+  for (size_t i = 0; i < plan.args.size(); ++i) {
+    SearchArgs& a = plan.args[i];
+    a.F = d_filters + plan.f_off[i];
+    if (a.records == 0) continue;
+    a.cta_total = reinterpret_cast<unsigned long long*>(d_ws + plan.ws_off[i]);
+    a.cta_overflow = a.cta_total + a.records;
+    a.region = reinterpret_cast<uint32_t*>(a.cta_overflow + a.records);
+  }
+}
+
+int batch_grid(const BatchPlan& plan, int dev, int* grid) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<int, size_t>, int>> cache;  // (dev, smem) -> CTAs per SM
+  int per_sm = -1;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& c : cache)
+      if (c.first.first == dev && c.first.second == plan.smem_scan) per_sm = c.second;
+  }
+  if (per_sm < 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hc_batch_scan_kernel, kThreads,
+                                                                  plan.smem_scan);
+    if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch)");
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache.size() < 256) cache.push_back({{dev, plan.smem_scan}, per_sm});
+  }
+  const DeviceInfo& di = device_info(dev);
+  *grid = static_cast<int>(std::min<unsigned long long>(
+      static_cast<unsigned long long>(std::max(per_sm, 1)) * di.sm_count,
+      std::max<unsigned long long>(plan.tiles.size(), 1)));
+  return HC_OK;
+}
+
+int launch_batch(const BatchLaunch& L, cudaStream_t stream) {
+  if (L.nq == 0) return HC_OK;
+  TimingToken t0 = timing_begin(kKindPreprocess, stream);
+  hc_batch_preprocess_kernel<<<static_cast<unsigned>(L.nq), kThreads, L.smem_pre, stream>>>(
+      const_cast<SearchArgs*>(L.args), L.counter);
+  cudaError_t e = cudaGetLastError();
+  timing_end(t0, stream);
+  if (e != cudaSuccess) return cuda_error(e, "hc_batch_preprocess_kernel launch");
+  if (L.ntiles == 0) {
+    g_launches.fetch_add(1);
+    return HC_OK;
+  }
+  TimingToken t1 = timing_begin(kKindBatch, stream);
+  hc_batch_scan_kernel<<<L.grid_scan, kThreads, L.smem_scan, stream>>>(L.args, L.tiles, L.ntiles,
+                                                                      L.counter, L.lay);
+  e = cudaGetLastError();
+  timing_end(t1, stream);
+  if (e != cudaSuccess) return cuda_error(e, "hc_batch_scan_kernel launch");
+  TimingToken t2 = timing_begin(kKindEmit, stream);
+  hc_batch_emit_kernel<<<static_cast<unsigned>(L.netiles * kEmitSplit), kThreads, L.smem_emit, stream>>>(
+      L.args, L.etiles);
+  e = cudaGetLastError();
+  timing_end(t2, stream);
+  if (e != cudaSuccess) return cuda_error(e, "hc_batch_emit_kernel launch");
+  g_launches.fetch_add(3);
+  return HC_OK;
+}
+
+int estimate_sigma(const uint8_t* const* y_dev, const uint64_t* n, size_t count,
+                   std::vector<double>* sigma, cudaStream_t stream) {
+  sigma->assign(count, 0.0);
+  std::vector<SigmaJob> jobs;
+  std::vector<size_t> idx;
+  for (size_t i = 0; i < count; ++i)
+    if (n[i] > 0 && y_dev[i] != nullptr) {
+      jobs.push_back({y_dev[i], n[i]});
+      idx.push_back(i);
+    }
+  if (jobs.empty()) return HC_OK;
+  SigmaJob* d_jobs = nullptr;
+  uint32_t* d_hist = nullptr;
+  int rc = dev_alloc(&d_jobs, jobs.size(), "cudaMalloc(sigma jobs)");
+  if (rc == HC_OK) rc = dev_alloc(&d_hist, jobs.size() * 256, "cudaMalloc(sigma histograms)");
+  std::vector<uint32_t> hist(jobs.size() * 256);
+  if (rc == HC_OK) {
+    cudaError_t e = cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(SigmaJob),
+                                    cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) {
+      hc_sigma_kernel<<<static_cast<unsigned>(jobs.size()), kThreads, 0, stream>>>(d_jobs, d_hist);
+      e = cudaGetLastError();
+      g_launches.fetch_add(1);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hist.data(), d_hist, hist.size() * 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) rc = cuda_error(e, "estimate_sigma");
+  }
+  cudaFree(d_jobs);
+  cudaFree(d_hist);
+  if (rc != HC_OK) return rc;
+  for (size_t k = 0; k < jobs.size(); ++k) {
+    double tot = 0, sq = 0;
+    for (int c = 0; c < 256; ++c) {
+      const double v = hist[k * 256 + c];
+      tot += v;
+      sq += v * v;
+    }
+    (*sigma)[idx[k]] = sq > 0 ? tot * tot / sq : 0.0;
+  }
+  return HC_OK;
+}
 
 struct Batch {
   uint32_t magic = kBatchMagic;
   int dev = -1;
-  size_t nq = 0;
-  std::vector<SearchArgs> host_args;
+  BatchPlan plan;
+  BatchLaunch launch;
   SearchArgs* d_args = nullptr;
   BatchTile* d_tiles = nullptr;
   EmitTile* d_etiles = nullptr;
   unsigned long long* d_counter = nullptr;
   uint32_t* d_filters = nullptr;
   uint8_t* d_ws = nullptr;
-  unsigned long long ntiles = 0, netiles = 0, records = 0;
-  size_t ws_bytes = 0;
-  BatchLayout lay{};
-  size_t smem_pre = 0, smem_scan = 0, smem_emit = 0;
-  int grid_scan = 0;
 
   ~Batch() {
     if (dev >= 0) {
@@ -220,10 +454,110 @@ Batch* as_batch(const hc_batch* b) {
   return (p != nullptr && p->magic == kBatchMagic) ? p : nullptr;
 }
 
-int set_kernel_smem(const void* fn, size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(bytes));
-  return e == cudaSuccess ? HC_OK : cuda_error(e, "cudaFuncSetAttribute(batch)");
+int create_batch(const hc_batch_query* qs, size_t nq, const hc_tuner* tuner, hc_batch** out,
+                 const char* who) {
+  clear_error();
+  if (out == nullptr) return set_error(HC_ERR_ARG, std::string(who) + ": out is NULL");
+  *out = nullptr;
+  if (qs == nullptr && nq > 0) return set_error(HC_ERR_ARG, std::string(who) + ": queries is NULL");
+  if (nq >= (size_t(1) << 31)) return set_error(HC_ERR_ARG, std::string(who) + ": too many queries");
+  const Tuner* t = nullptr;
+  if (tuner != nullptr && (t = as_tuner(tuner)) == nullptr)
+    return set_error(HC_ERR_ARG, std::string(who) + ": invalid tuner");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+
+  // parameters: given (q > 0) or tuned for the text's alphabet size
+  std::vector<const uint8_t*> est_y;
+  std::vector<uint64_t> est_n;
+  std::vector<size_t> est_i;
+  for (size_t i = 0; i < nq; ++i)
+    if (qs[i].q == 0 && qs[i].sigma <= 0) {
+      est_y.push_back(qs[i].y_dev);
+      est_n.push_back(qs[i].n);
+      est_i.push_back(i);
+    }
+  std::vector<double> est;
+  if (!est_i.empty()) {
+    int rc = estimate_sigma(est_y.data(), est_n.data(), est_i.size(), &est, nullptr);
+    if (rc != HC_OK) return rc;
+  }
+  Batch* b = new (std::nothrow) Batch();
+  if (b == nullptr) return set_error(HC_ERR_NOMEM, std::string(who) + ": out of host memory");
+  BatchPlan& plan = b->plan;
+  plan.args.reserve(nq);
+  size_t k = 0;
+  for (size_t i = 0; i < nq; ++i) {
+    const hc_batch_query& Q = qs[i];
+    QueryParams p;
+    if (Q.q > 0) {
+      p.q = Q.q;
+      p.alpha = Q.alpha;
+      p.lane_bytes = Q.lane_bytes;
+      p.mode = Q.mode;
+    } else if (Q.q == 0) {
+      double sigma = Q.sigma;
+      if (Q.sigma <= 0) sigma = est[k++];
+      p = tuner_lookup(t, sigma, Q.m);
+      if (Q.lane_bytes > 0) p.lane_bytes = Q.lane_bytes;
+      if (Q.mode != HC_MODE_AUTO) p.mode = Q.mode;
+    } else {
+      p.q = Q.q;  // negative: rejected below
+    }
+    int rc = plan_add_query(plan, Q, i, p, who);
+    if (rc != HC_OK) {
+      delete b;
+      return rc;
+    }
+  }
+  int rc = plan_finish(plan, dev, who);
+  if (rc != HC_OK) {
+    delete b;
+    return rc;
+  }
+  b->dev = dev;
+  if (rc == HC_OK) rc = dev_alloc(&b->d_args, nq, "cudaMalloc(batch args)");
+  if (rc == HC_OK) rc = dev_alloc(&b->d_tiles, plan.tiles.size(), "cudaMalloc(batch tiles)");
+  if (rc == HC_OK) rc = dev_alloc(&b->d_etiles, plan.etiles.size(), "cudaMalloc(batch emit tiles)");
+  if (rc == HC_OK) rc = dev_alloc(&b->d_counter, 1, "cudaMalloc(batch counter)");
+  if (rc == HC_OK) rc = dev_alloc(&b->d_filters, plan.filter_words, "cudaMalloc(batch filters)");
+  if (rc == HC_OK) rc = dev_alloc(&b->d_ws, plan.ws_bytes, "cudaMalloc(batch workspace)");
+  if (rc != HC_OK) {
+    delete b;
+    return rc;
+  }
+  plan_bind(plan, b->d_filters, b->d_ws);
+  e = cudaMemcpy(b->d_args, plan.args.data(), nq * sizeof(SearchArgs), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !plan.tiles.empty())
+    e = cudaMemcpy(b->d_tiles, plan.tiles.data(), plan.tiles.size() * sizeof(BatchTile),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !plan.etiles.empty())
+    e = cudaMemcpy(b->d_etiles, plan.etiles.data(), plan.etiles.size() * sizeof(EmitTile),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_error(e, "cudaMemcpy(batch tables)");
+  }
+  BatchLaunch& L = b->launch;
+  L.args = b->d_args;
+  L.tiles = b->d_tiles;
+  L.etiles = b->d_etiles;
+  L.counter = b->d_counter;
+  L.nq = nq;
+  L.ntiles = plan.tiles.size();
+  L.netiles = plan.etiles.size();
+  L.lay = plan.lay;
+  L.smem_pre = plan.smem_pre;
+  L.smem_scan = plan.smem_scan;
+  L.smem_emit = plan.smem_emit;
+  rc = batch_grid(plan, dev, &L.grid_scan);
+  if (rc != HC_OK) {
+    delete b;
+    return rc;
+  }
+  *out = reinterpret_cast<hc_batch*>(b);
+  return HC_OK;
 }
 
 }  // namespace
@@ -234,213 +568,55 @@ using namespace hc;
 extern "C" {
 
 int hc_batch_create(const hc_batch_query* qs, size_t nq, hc_batch** out) {
-  clear_error();
-  if (out == nullptr) return set_error(HC_ERR_ARG, "hc_batch_create: out is NULL");
-  *out = nullptr;
-  if (qs == nullptr && nq > 0) return set_error(HC_ERR_ARG, "hc_batch_create: queries is NULL");
-  if (nq >= (size_t(1) << 31)) return set_error(HC_ERR_ARG, "hc_batch_create: too many queries");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
-  const DeviceInfo& di = device_info(dev);
-  Batch* b = new (std::nothrow) Batch();
-  if (b == nullptr) return set_error(HC_ERR_NOMEM, "hc_batch_create: out of host memory");
-  b->nq = nq;
-  b->host_args.resize(nq);
-  std::vector<BatchTile> tiles;
-  std::vector<EmitTile> etiles;
-  size_t filter_words = 0, ws_bytes = 0;
-  std::vector<size_t> f_off(nq), ws_off(nq);
-  uint32_t f_max = 0, x_max = 0, ring_max = 0;
-  const int stages = 2;
+  return create_batch(qs, nq, nullptr, out, "hc_batch_create");
+}
 
-  for (size_t i = 0; i < nq; ++i) {
-    const hc_batch_query& Q = qs[i];
-    char msg[160];
-    if (Q.x_dev == nullptr || Q.count_dev == nullptr || (Q.y_dev == nullptr && Q.n > 0) ||
-        (Q.pos_dev == nullptr && Q.cap > 0) || !aligned8(Q.pos_dev) || !aligned8(Q.count_dev)) {
-      std::snprintf(msg, sizeof msg, "hc_batch_create: query %zu: null or misaligned pointer", i);
-      delete b;
-      return set_error(HC_ERR_ARG, msg);
-    }
-    if (Q.m < 1 || Q.q < 1 || Q.q > kMaxQ || static_cast<uint64_t>(Q.q) > Q.m || Q.alpha < 1 ||
-        Q.alpha > kMaxAlpha || Q.m > (uint64_t(1) << 30)) {
-      std::snprintf(msg, sizeof msg,
-                    "hc_batch_create: query %zu: need m >= 1, 1 <= q <= min(m, 8), 1 <= alpha <= 15", i);
-      delete b;
-      return set_error(HC_ERR_ARG, msg);
-    }
-    SearchArgs& a = b->host_args[i];
-    a = SearchArgs{};
-    a.status = status_word();
-    a.y = Q.y_dev;
-    a.n = Q.n;
-    a.x = Q.x_dev;
-    a.m = static_cast<int>(Q.m);
-    a.q = Q.q;
-    a.s = Q.alpha / Q.q;
-    a.fwords = 1u << Q.alpha;
-    a.mask = a.fwords - 1u;
-    a.pos = reinterpret_cast<unsigned long long*>(Q.pos_dev);
-    a.cap = Q.pos_dev ? Q.cap : 0;
-    a.count_out = reinterpret_cast<unsigned long long*>(Q.count_dev);
-    {
-      int g = 1;
-      while (g < 4 && g < a.q && a.s * g <= 7) ++g;
-      a.g0 = g;
-      for (int k = 0; k < g; ++k) a.w0 |= (1u << (a.s * k)) << (8 * k);
-      for (int k = 0; k < a.q - g && k < 4; ++k) a.w1 |= (1u << (a.s * k)) << (8 * k);
-    }
-    f_off[i] = filter_words;
-    filter_words += (a.fwords + 3u) & ~3u;
-    f_max = std::max(f_max, a.fwords * 4u);
-    if (Q.n < Q.m) {
-      a.records = 0;
-      continue;
-    }
-    const int shift = a.m - a.q + 1;
-    const bool direct = Q.mode == HC_MODE_DIRECT ||
-                        (Q.mode != HC_MODE_STAGED && (shift >= 200 || Q.m > 16384));
-    int L = Q.lane_bytes;
-    if (L <= 0) L = direct ? std::min(4096, std::max(64, shift)) : 4 * std::min(std::max(16, shift) | 1, 47);
-    L = std::min(L, 4096);
-    a.L = L;
-    a.C = 32u * static_cast<uint32_t>(L);
-    a.stages = direct ? 0 : stages;
-    a.head = static_cast<int>(reinterpret_cast<uintptr_t>(Q.y_dev) & 15u);
-    a.stage_bytes = direct ? 0u : static_cast<uint32_t>(((16 + a.C + Q.m - 1 + 15) & ~uint64_t(15)) + 64);
-    a.x_smem = Q.m <= 4096 ? static_cast<uint32_t>((Q.m + 15) & ~uint64_t(15)) : 0u;
-    x_max = std::max(x_max, a.x_smem);
-    ring_max = std::max(ring_max, static_cast<uint32_t>(a.stages) * a.stage_bytes);
-    a.nwin = Q.n - Q.m + 1;
-    a.num_chunks = (a.nwin + a.C - 1) / a.C;
-    a.chunks_per_cta = std::max<unsigned long long>(1, (kTileTextBytes + a.C - 1) / a.C);
-    a.records = (a.num_chunks + a.chunks_per_cta - 1) / a.chunks_per_cta;
-    const unsigned long long spill =
-        a.cap == 0 ? 0 : std::min<unsigned long long>(a.nwin, std::max<unsigned long long>(a.cap, 4096));
-    a.region_entries = (std::max<unsigned long long>(1, (spill + a.records - 1) / a.records) + 3) & ~3ull;
-    ws_off[i] = ws_bytes;
-    ws_bytes += a.records * 16 + a.records * a.region_entries * 4;
-    const unsigned long long groups = (a.records + 15) / 16;
-    a.emit_group = (a.records + groups - 1) / groups;
-    for (unsigned long long r = 0; r < a.records; r += kWarps)
-      tiles.push_back({static_cast<uint32_t>(i), static_cast<uint32_t>(r)});
-    for (unsigned long long g = 0; (g * a.emit_group) < a.records; ++g)
-      etiles.push_back({static_cast<uint32_t>(i), static_cast<uint32_t>(g)});
-    b->records += a.records;
-  }
-
-  b->dev = dev;
-  int rc = HC_OK;
-  if (rc == HC_OK) rc = dev_alloc(&b->d_args, nq, "cudaMalloc(batch args)");
-  if (rc == HC_OK) rc = dev_alloc(&b->d_tiles, tiles.size(), "cudaMalloc(batch tiles)");
-  if (rc == HC_OK) rc = dev_alloc(&b->d_etiles, etiles.size(), "cudaMalloc(batch emit tiles)");
-  if (rc == HC_OK) rc = dev_alloc(&b->d_counter, 1, "cudaMalloc(batch counter)");
-  if (rc == HC_OK) rc = dev_alloc(&b->d_filters, filter_words, "cudaMalloc(batch filters)");
-  if (rc == HC_OK) rc = dev_alloc(&b->d_ws, ws_bytes, "cudaMalloc(batch workspace)");
-  if (rc != HC_OK) {
-    delete b;
-    return rc;
-  }
-  for (size_t i = 0; i < nq; ++i) {
-    SearchArgs& a = b->host_args[i];
-    a.F = b->d_filters + f_off[i];
-    if (a.records == 0) continue;
-    a.cta_total = reinterpret_cast<unsigned long long*>(b->d_ws + ws_off[i]);
-    a.cta_overflow = a.cta_total + a.records;
-    a.region = reinterpret_cast<uint32_t*>(a.cta_overflow + a.records);
-  }
-  b->ntiles = tiles.size();
-  b->netiles = etiles.size();
-  b->ws_bytes = ws_bytes;
-  e = cudaMemcpy(b->d_args, b->host_args.data(), nq * sizeof(SearchArgs), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !tiles.empty())
-    e = cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !etiles.empty())
-    e = cudaMemcpy(b->d_etiles, etiles.data(), etiles.size() * sizeof(EmitTile), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    delete b;
-    return cuda_error(e, "cudaMemcpy(batch tables)");
-  }
-
-  b->lay.f_bytes = (f_max + 15u) & ~15u;
-  b->lay.x_bytes = x_max;
-  b->lay.ring_bytes = ring_max;
-  b->smem_pre = f_max;
-  b->smem_scan = size_t(b->lay.f_bytes) + b->lay.x_bytes + size_t(kSlots) * kThreads * 4 +
-                 size_t(kWarps) * b->lay.ring_bytes;
-  b->smem_emit = size_t(b->lay.f_bytes) + size_t(kSlots) * kThreads * 4;
-  if (b->smem_scan + 2048 > di.smem_optin) {
-    delete b;
-    return set_error(HC_ERR_ARG, "hc_batch_create: filter and staging buffers exceed shared memory");
-  }
-  rc = set_kernel_smem(reinterpret_cast<const void*>(hc_batch_preprocess_kernel), std::max<size_t>(b->smem_pre, 1));
-  if (rc == HC_OK) rc = set_kernel_smem(reinterpret_cast<const void*>(hc_batch_scan_kernel), b->smem_scan);
-  if (rc == HC_OK) rc = set_kernel_smem(reinterpret_cast<const void*>(hc_batch_emit_kernel), b->smem_emit);
-  int per_sm = 0;
-  if (rc == HC_OK) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hc_batch_scan_kernel, kThreads, b->smem_scan);
-    if (e != cudaSuccess) rc = cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch)");
-  }
-  if (rc != HC_OK) {
-    delete b;
-    return rc;
-  }
-  b->grid_scan = static_cast<int>(std::min<unsigned long long>(
-      std::max(per_sm, 1) * static_cast<unsigned long long>(di.sm_count), std::max<unsigned long long>(b->ntiles, 1)));
-  *out = reinterpret_cast<hc_batch*>(b);
-  return HC_OK;
+int hc_batch_create_tuned(const hc_batch_query* qs, size_t nq, const hc_tuner* tuner, hc_batch** out) {
+  return create_batch(qs, nq, tuner, out, "hc_batch_create_tuned");
 }
 
 int hc_batch_run(hc_batch* bp, hc_stream_t stream_) {
   clear_error();
   Batch* b = as_batch(bp);
   if (b == nullptr) return set_error(HC_ERR_ARG, "hc_batch_run: invalid batch");
-  if (b->nq == 0) return HC_OK;
+  if (b->launch.nq == 0) return HC_OK;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev != b->dev) return set_error(HC_ERR_STATE, "hc_batch_run: batch belongs to another device");
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  TimingToken t0 = timing_begin(kKindPreprocess, stream);
-  hc_batch_preprocess_kernel<<<static_cast<unsigned>(b->nq), kThreads, b->smem_pre, stream>>>(
-      b->d_args, b->d_counter);
-  cudaError_t e = cudaGetLastError();
-  timing_end(t0, stream);
-  if (e != cudaSuccess) return cuda_error(e, "hc_batch_preprocess_kernel launch");
-  if (b->ntiles > 0) {
-    TimingToken t1 = timing_begin(kKindBatch, stream);
-    hc_batch_scan_kernel<<<b->grid_scan, kThreads, b->smem_scan, stream>>>(
-        b->d_args, b->d_tiles, b->ntiles, b->d_counter, b->lay);
-    e = cudaGetLastError();
-    timing_end(t1, stream);
-    if (e != cudaSuccess) return cuda_error(e, "hc_batch_scan_kernel launch");
-    TimingToken t2 = timing_begin(kKindEmit, stream);
-    hc_batch_emit_kernel<<<static_cast<unsigned>(b->netiles * kEmitSplit), kThreads, b->smem_emit, stream>>>(
-        b->d_args, b->d_etiles);
-    e = cudaGetLastError();
-    timing_end(t2, stream);
-    if (e != cudaSuccess) return cuda_error(e, "hc_batch_emit_kernel launch");
-    g_launches.fetch_add(3);
-  } else {
-    g_launches.fetch_add(1);
-  }
-  return HC_OK;
+  return launch_batch(b->launch, reinterpret_cast<cudaStream_t>(stream_));
 }
 
 int hc_batch_info(const hc_batch* bp, uint64_t* tiles, uint64_t* records, uint64_t* workspace_bytes) {
   Batch* b = as_batch(bp);
   if (b == nullptr) return set_error(HC_ERR_ARG, "hc_batch_info: invalid batch");
-  if (tiles) *tiles = b->ntiles;
-  if (records) *records = b->records;
-  if (workspace_bytes) *workspace_bytes = b->ws_bytes;
+  if (tiles) *tiles = b->plan.tiles.size();
+  if (records) *records = b->plan.records;
+  if (workspace_bytes) *workspace_bytes = b->plan.ws_bytes;
+  return HC_OK;
+}
+
+int hc_batch_params(const hc_batch* bp, size_t query, hc_tune_entry* out) {
+  clear_error();
+  Batch* b = as_batch(bp);
+  if (b == nullptr || query >= b->plan.args.size() || out == nullptr)
+    return set_error(HC_ERR_ARG, "hc_batch_params: invalid batch, query or output");
+  const QueryParams& p = b->plan.params[query];
+  const SearchArgs& a = b->plan.args[query];
+  *out = hc_tune_entry{};
+  out->m = static_cast<uint64_t>(a.m);
+  out->q = p.q;
+  out->alpha = p.alpha;
+  out->lane_bytes = a.records ? a.L : p.lane_bytes;
+  out->mode = a.records == 0 ? p.mode : (a.stages > 0 ? HC_MODE_STAGED : HC_MODE_DIRECT);
   return HC_OK;
 }
 
 int hc_batch_filter(const hc_batch* bp, size_t query, uint32_t* F, size_t nwords, uint32_t* hv) {
   clear_error();
   Batch* b = as_batch(bp);
-  if (b == nullptr || query >= b->nq) return set_error(HC_ERR_ARG, "hc_batch_filter: invalid batch or query");
-  const SearchArgs& a = b->host_args[query];
+  if (b == nullptr || query >= b->plan.args.size())
+    return set_error(HC_ERR_ARG, "hc_batch_filter: invalid batch or query");
+  const SearchArgs& a = b->plan.args[query];
   if (F != nullptr) {
     if (nwords < a.fwords) return set_error(HC_ERR_ARG, "hc_batch_filter: F holds fewer than 2^alpha words");
     cudaError_t e = cudaMemcpy(F, a.F, size_t(a.fwords) * 4, cudaMemcpyDeviceToHost);

@@ -195,3 +195,52 @@ def test_batch_rejects_bad_query(hc):
         with pytest.raises(hc.HCError) as ei:
             hc.hc_batch_create([qd])
         assert ei.value.code == hc.HC_ERR_ARG
+
+
+def test_tuner_calibration_and_tuned_batch(hc):
+    """Calibrate a small table on the device, then run q = 0 queries whose
+    alphabet size is measured from their texts: each query runs with the
+    tuned cell of its alphabet, its filter equals the oracle's for those
+    parameters, and its positions equal the oracle's."""
+    t = hc.HCTuner()
+    t.calibrate([4, 95], [8, 64], text_bytes=8 << 20, seed=3)
+    ent = t.entries()
+    assert [(e["sigma"], e["m"]) for e in ent] == [(4, 8), (4, 64), (95, 8), (95, 64)]
+    for e in ent:
+        assert 1 <= e["q"] <= min(8, e["m"]) and 8 <= e["alpha"] <= 13, e
+        assert e["mode"] in (1, 2) and 1 <= e["lane_bytes"] <= 4096 and e["gbps"] > 0, e
+    rng = np.random.default_rng(12)
+    qs, dq = [], []
+    for i in range(24):
+        sigma = 4 if i % 2 else 95
+        n = int(rng.integers(5000, 400_000))
+        m = int(rng.choice([5, 8, 13, 40, 64, 100]))
+        y = hi.uniform_text(n, sigma, seed=50 + i)
+        x, _ = hi.extract_pattern(y, m, rng)
+        want = oracle.naive_search(x, y)
+        qs.append((x, y, sigma, want))
+        dq.append(dict(x_dev=torch.from_numpy(x).cuda(), y_dev=torch.from_numpy(y).cuda(), q=0,
+                       sigma=0 if i % 3 else sigma,
+                       pos_dev=torch.full((want.size + 2,), -1, dtype=torch.int64, device="cuda"),
+                       count_dev=torch.full((1,), -1, dtype=torch.int64, device="cuda")))
+    b = hc.hc_batch_create_tuned(dq, t)
+    b.run()
+    torch.cuda.synchronize()
+    hc.hc_check_status()
+    for i, (x, y, sigma, want) in enumerate(qs):
+        p = b.params(i)
+        tuned = t.lookup(sigma, x.size)
+        assert (p["q"], p["alpha"]) == (tuned["q"], tuned["alpha"]), (i, p, tuned)
+        assert int(dq[i]["count_dev"].item()) == want.size, i
+        got = dq[i]["pos_dev"][:want.size].cpu().numpy().view(np.uint64)
+        assert np.array_equal(got, want), i
+        F, hv = b.filter(i, p["alpha"])
+        ref = oracle.preprocess(x, p["q"], p["alpha"])
+        assert np.array_equal(F, ref["F"]) and hv == ref["hv"], i
+    b.destroy()
+    # without a tuner, q = 0 takes the paper's choice
+    b = hc.hc_batch_create(dq)
+    for i, (x, y, sigma, want) in enumerate(qs):
+        assert (b.params(i)["q"], b.params(i)["alpha"]) == hi.paper_q_alpha(sigma, x.size), i
+    b.destroy()
+    t.free()
