@@ -43,6 +43,7 @@ if ROOT not in sys.path:
 import hc_inputs as hi  # noqa: E402
 
 GB = 1e9
+SERVED_RATES_DEFAULT = (1000, 10000, 50000)
 METRIC = "text GB/s searched (device-timed), plain HC sweep"
 UNIT = "GB/s"
 
@@ -58,9 +59,12 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["sweep", "batched"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "batched", "served"], default="sweep",
                     help="sweep: the plain-HC sweep (default); batched: 4096 queries in one "
-                         "graph-captured batch vs. one plain launch per query")
+                         "graph-captured batch vs. one plain launch per query; served: Poisson "
+                         "request streams into the server vs. a plain per-request server")
+    ap.add_argument("--served-rates", type=int, nargs="+", default=list(SERVED_RATES_DEFAULT))
+    ap.add_argument("--served-seconds", type=float, default=2.0)
     ap.add_argument("--batch-queries", type=int, default=4096)
     ap.add_argument("--tune-text-bytes", type=int, default=256 << 20,
                     help="calibration text per alphabet size (batched workload)")
@@ -525,6 +529,99 @@ def run_batched(args, rank, world, local_rank):
         f.free()
 
 
+SERVED_TUNE_MS = (2, 4, 8, 16, 32, 64, 128, 256, 512, 1024)
+
+
+def _pct(v, p):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), p)) if len(v) else None
+
+
+def run_served(args, rank, world, local_rank):
+    """The served workload: 64 device-resident texts (n log-uniform 1 KiB to
+    16 MiB, sigma from {4, 20, 95}), Poisson request streams at 1k, 10k and
+    50k requests/s (m log-uniform 2 to 1024, each pattern copied from its
+    text), replayed natively into an hc_server (continuous batching, 32 GiB
+    admission, tuned parameters) and into a plain server (one search launch
+    per request, same parameters).  Reports per load p50/p99 latency (from
+    the scheduled arrival to the result on the host), achieved requests/s
+    and aggregate text GB/s (sum of n over the span from first arrival to
+    last result), and whether every count matches between the two."""
+    import torch
+    import paper_2310_15711_gb300 as hc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    hc.build()
+    hc.lib()
+    texts = hi.served_texts(64)
+    ydev = [hi.device_uniform_text(n, sigma, seed, dev) for n, sigma, seed in texts]
+    yhost = [y.cpu().numpy() for y in ydev]
+    tuner = hc.HCTuner()
+    t0 = time.perf_counter()
+    tuner.calibrate([4, 20, 95], SERVED_TUNE_MS, text_bytes=16 << 20, seed=12)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    loads = []
+    for rate in args.served_rates:
+        count = max(200, int(rate * args.served_seconds))
+        stream = hi.served_requests(texts, count, float(rate), seed=6 + rate)
+        reqs = [(0, yhost[ti][off:off + m]) for _, ti, m, off in stream]
+        arrivals = [a for a, _, _, _ in stream]
+        entry = {"offered_req_per_s": rate, "requests": count}
+        counts = {}
+        for plain in (0, 1):
+            srv = hc.HCServer(hc.ServerConfig(plain=plain), tuner)
+            tids = [srv.add_text(y, sigma=texts[i][1]) for i, y in enumerate(ydev)]
+            rq = [(tids[ti], x) for (_, ti, _, _), (_, x) in zip(stream, reqs)]
+            l0 = hc.hc_kernel_launches()
+            ids = srv.replay(rq, arrivals)
+            srv.drain()
+            res = []
+            while len(res) < count:
+                res += srv.poll(65536, wait_us=100_000, positions=False)
+            st = srv.stats()
+            launches = hc.hc_kernel_launches() - l0
+            srv.destroy()
+            pos = {rid: k for k, rid in enumerate(ids)}
+            lat = [(r["done_ns"] - r["submit_ns"]) / 1e3 for r in res]
+            span = (max(r["done_ns"] for r in res) - min(r["submit_ns"] for r in res)) / 1e9
+            nbytes = sum(texts[stream[pos[r["id"]]][1]][0] for r in res)
+            bad = sum(1 for r in res if r["status"] not in (hc.HC_OK, hc.HC_ERR_CAPACITY))
+            counts[plain] = {pos[r["id"]]: r["count"] for r in res}
+            entry["plain" if plain else "batched"] = {
+                "p50_us": round(_pct(lat, 50), 1), "p99_us": round(_pct(lat, 99), 1),
+                "mean_us": round(float(np.mean(lat)), 1),
+                "achieved_req_per_s": round(count / span, 1),
+                "GBps": round(nbytes / span / GB, 3),
+                "batches": st["batches"], "max_batch": st["max_batch"],
+                "mean_batch": round(count / max(st["batches"], 1), 2),
+                "peak_admitted_MiB": round(st["peak_inflight_bytes"] / 2 ** 20, 2),
+                "errors": bad, "gpu_launches": launches,
+            }
+        entry["counts_equal"] = counts[0] == counts[1]
+        entry["p99_ratio_plain_over_batched"] = round(
+            entry["plain"]["p99_us"] / max(entry["batched"]["p99_us"], 1e-9), 3)
+        loads.append(entry)
+    top = loads[-1]
+    line = {
+        "metric": "served HC: aggregate text GB/s at the highest offered load (p50/p99 latency per load)",
+        "value": top["batched"]["GBps"], "unit": UNIT, "n_gpus": 1,
+        "steps": len(loads), "warmup": 0, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "served HC", "texts": len(texts),
+                   "text_n": "log-uniform 1 KiB .. 16 MiB", "sigma": "{4, 20, 95}",
+                   "m": "log-uniform 2 .. 1024", "arrivals": "Poisson",
+                   "offered_req_per_s": list(args.served_rates), "seconds_per_load": args.served_seconds,
+                   "admission_GiB": 32, "q_alpha": "autotuned (sigma in {4, 20, 95}, m 2 .. 1024)",
+                   "latency": "scheduled arrival -> result copied on the host"},
+        "p50_us": top["batched"]["p50_us"], "p99_us": top["batched"]["p99_us"],
+        "loads": loads, "tune_s": round(tune_s, 2),
+    }
+    print(json.dumps(line), flush=True)
+    tuner.free()
+
+
 def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream):
     """One sweep step through hc_search (the synchronous C-ABI call): per
     sigma the text is copied from pinned host memory to the device, every
@@ -571,6 +668,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, rank, world, local_rank)
+        return
+    if args.workload == "served":
+        run_served(args, rank, world, local_rank)
         return
     if world > 1:
         import torch

@@ -83,6 +83,19 @@ SIGNATURES = {
     "hc_tuner_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "hc_tuner_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "hc_tuner_free": (None, [_vp]),
+    "hc_server_create": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
+    "hc_server_add_text": (ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_uint32)]),
+    "hc_server_text_info": (ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "hc_server_submit": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "hc_server_replay": (ctypes.c_int, [_vp, _vp, _sz, ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "hc_server_poll": (ctypes.c_int, [_vp, _vp, _sz, ctypes.POINTER(_sz), ctypes.c_int64]),
+    "hc_server_release": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "hc_server_drain": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "hc_server_get_stats": (ctypes.c_int, [_vp, _vp]),
+    "hc_server_destroy": (None, [_vp]),
     "hc_check_status": (ctypes.c_int, [_vp]),
     "hc_kernel_launches": (ctypes.c_uint64, []),
     "hc_timing_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -438,6 +451,150 @@ class HCBatch:
     def destroy(self):
         if self._h is not None and _lib is not None:
             _lib.hc_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class ServerConfig(ctypes.Structure):
+    """hc_server_config (zero = default)."""
+    _fields_ = [("struct_size", _sz), ("mem_limit", ctypes.c_uint64), ("max_inflight", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("default_cap", ctypes.c_uint64), ("plain", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+    def __init__(self, mem_limit=0, max_inflight=0, max_batch=0, default_cap=0, plain=0):
+        super().__init__(ctypes.sizeof(ServerConfig), mem_limit, max_inflight, max_batch, default_cap,
+                         plain, 0)
+
+
+class ServerRequest(ctypes.Structure):
+    """hc_server_request."""
+    _fields_ = [("text", ctypes.c_uint32), ("q", ctypes.c_int), ("alpha", ctypes.c_int),
+                ("lane_bytes", ctypes.c_int), ("mode", ctypes.c_int), ("x", _vp),
+                ("m", ctypes.c_uint64), ("cap", ctypes.c_uint64)]
+
+
+class ServerResult(ctypes.Structure):
+    """hc_server_result."""
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("text", ctypes.c_uint32),
+                ("q", ctypes.c_int), ("alpha", ctypes.c_int), ("count", ctypes.c_uint64),
+                ("npos", ctypes.c_uint64), ("pos", ctypes.POINTER(ctypes.c_uint64)),
+                ("submit_ns", ctypes.c_uint64), ("start_ns", ctypes.c_uint64),
+                ("done_ns", ctypes.c_uint64), ("batch", ctypes.c_uint64),
+                ("batch_size", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    """hc_server_stats."""
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "submitted", "completed", "batches", "rejected", "admission_waits", "max_batch", "pending",
+        "inflight_bytes", "peak_inflight_bytes", "text_bytes", "mem_limit")]
+
+
+class HCServer:
+    """An hc_server: resident texts, a request queue and a worker thread that
+    runs queued requests as batches on up to max_inflight streams."""
+
+    def __init__(self, config: ServerConfig | None = None, tuner: HCTuner | None = None):
+        h = _vp()
+        _check(lib().hc_server_create(ctypes.byref(config) if config is not None else None,
+                                      tuner.handle if tuner is not None else None, ctypes.byref(h)),
+               "hc_server_create")
+        self._h = h
+        self._keep = [tuner]
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("server has been destroyed")
+        return self._h
+
+    def add_text(self, y, sigma: int = 0) -> int:
+        """Registers a text: a uint8 CUDA tensor (kept by reference; it must
+        outlive the server) or host bytes / numpy array (copied)."""
+        tid = ctypes.c_uint32()
+        if hasattr(y, "is_cuda") and y.is_cuda:
+            self._keep.append(y)
+            _check(lib().hc_server_add_text(self.handle, _dev_ptr(y), y.numel(), 1, int(sigma),
+                                            ctypes.byref(tid)), "hc_server_add_text")
+        else:
+            b = _bytes_arg(y)
+            buf = ctypes.create_string_buffer(b, len(b)) if b else None
+            _check(lib().hc_server_add_text(self.handle, ctypes.cast(buf, _vp) if buf is not None else None,
+                                            len(b), 0, int(sigma), ctypes.byref(tid)), "hc_server_add_text")
+        return tid.value
+
+    def text_info(self, text_id: int) -> dict:
+        n, sg = ctypes.c_uint64(), ctypes.c_double()
+        _check(lib().hc_server_text_info(self.handle, int(text_id), ctypes.byref(n), ctypes.byref(sg)),
+               "hc_server_text_info")
+        return {"n": n.value, "sigma": sg.value}
+
+    @staticmethod
+    def _request(text_id, x, q=0, alpha=0, cap=0, lane_bytes=0, mode=0):
+        xb = _bytes_arg(x)
+        buf = ctypes.create_string_buffer(xb, len(xb)) if xb else None
+        r = ServerRequest(int(text_id), int(q), int(alpha), int(lane_bytes), int(mode),
+                          ctypes.cast(buf, _vp) if buf is not None else None, len(xb), int(cap))
+        return r, buf
+
+    def submit(self, text_id: int, x, q: int = 0, alpha: int = 0, cap: int = 0, lane_bytes: int = 0,
+               mode: int = 0) -> int:
+        r, buf = self._request(text_id, x, q, alpha, cap, lane_bytes, mode)
+        rid = ctypes.c_uint64()
+        _check(lib().hc_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid)), "hc_server_submit")
+        return rid.value
+
+    def replay(self, requests, arrival_s) -> list:
+        """requests: list of (text_id, x[, q, alpha, cap]); arrival_s: their
+        arrival offsets in seconds (non-decreasing).  Submits each at its time
+        from this thread (the GIL is released) and returns the ids."""
+        n = len(requests)
+        arr = (ServerRequest * max(n, 1))()
+        keep = []
+        for i, rq in enumerate(requests):
+            r, buf = self._request(*rq)
+            arr[i] = r
+            keep.append(buf)
+        t = (ctypes.c_uint64 * max(n, 1))(*[int(round(a * 1e9)) for a in arrival_s])
+        ids = (ctypes.c_uint64 * max(n, 1))()
+        _check(lib().hc_server_replay(self.handle, ctypes.cast(arr, _vp), n, t, ids), "hc_server_replay")
+        return list(ids)[:n]
+
+    def poll(self, max_results: int = 1024, wait_us: int = 0, positions: bool = True) -> list:
+        """Completed results as dicts (positions copied to numpy uint64 and
+        the library's copy released)."""
+        out = (ServerResult * max_results)()
+        got = _sz()
+        _check(lib().hc_server_poll(self.handle, out, max_results, ctypes.byref(got), int(wait_us)),
+               "hc_server_poll")
+        res = []
+        for i in range(got.value):
+            r = out[i]
+            d = {k: getattr(r, k) for k in ("id", "status", "text", "q", "alpha", "count", "npos",
+                                            "submit_ns", "start_ns", "done_ns", "batch", "batch_size")}
+            if positions:
+                d["pos"] = (np.ctypeslib.as_array(r.pos, shape=(r.npos,)).copy() if r.npos
+                            else np.zeros(0, np.uint64))
+            _check(lib().hc_server_release(self.handle, r.id), "hc_server_release")
+            res.append(d)
+        return res
+
+    def drain(self, timeout_ms: int = -1):
+        _check(lib().hc_server_drain(self.handle, int(timeout_ms)), "hc_server_drain")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().hc_server_get_stats(self.handle, ctypes.byref(s)), "hc_server_get_stats")
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def destroy(self):
+        if self._h is not None and _lib is not None:
+            _lib.hc_server_destroy(self._h)
         self._h = None
 
     def __del__(self):

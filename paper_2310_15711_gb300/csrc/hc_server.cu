@@ -444,8 +444,8 @@ void Server::run() {
       if (s.busy) any_busy = true;
       else if (free_slot == nullptr) free_slot = &s;
     }
-    if (stop && !any_busy && (pending.empty() || fatal != HC_OK)) break;
-    if (free_slot != nullptr && !pending.empty() && fatal == HC_OK) {
+    if (stop && !any_busy) break;  // queued requests are cancelled below
+    if (free_slot != nullptr && !pending.empty() && fatal == HC_OK && !stop) {
       std::vector<Req*> b = take_batch();
       if (!b.empty()) {
         Slot& s = *free_slot;
@@ -663,7 +663,9 @@ int make_request(Server* s, const hc_server_request& q, uint64_t submit_ns, Req*
   r->y = t.y;
   r->n = t.n;
   r->x.assign(q.x, q.x + q.m);
-  r->cap = q.cap ? q.cap : s->cfg.default_cap;
+  // positions kept: at most one per window start (bounds the result arena)
+  const uint64_t nwin = t.n >= q.m ? t.n - q.m + 1 : 0;
+  r->cap = std::min<uint64_t>(q.cap ? q.cap : s->cfg.default_cap, nwin);
   if (q.q == 0) {
     r->p = tuner_lookup(s->tuner, t.sigma, q.m);
   } else {
