@@ -37,6 +37,10 @@ namespace {
 
 constexpr uint32_t kBatchMagic = 0x48434231u;  // "HCB1"
 constexpr unsigned long long kTileTextBytes = 64ull << 10;  // text per record, about
+// Spill entries per query at least (as positions): records whose share
+// overflows are re-scanned by the emit kernel, so the floor keeps dense
+// queries with a small cap from re-scanning most of their records.
+constexpr unsigned long long kMinSpill = 1ull << 15;
 
 // h(x[i .. i+q-1]) by Horner's rule from the last byte down (Eq. 3, Eq. 4).
 __device__ __forceinline__ uint32_t pattern_hash(const uint8_t* x, int i, int q, int s,
@@ -221,8 +225,13 @@ int init_batch_kernels(int dev) {
 
 }  // namespace
 
+unsigned long long record_bytes_for(unsigned long long total_text, int dev) {
+  const unsigned long long warps = static_cast<unsigned long long>(device_info(dev).sm_count) * 16;
+  return std::min<unsigned long long>(kTileTextBytes, std::max<unsigned long long>(1, total_text / warps));
+}
+
 int plan_add_query(BatchPlan& plan, const hc_batch_query& Q, size_t i, const QueryParams& p,
-                   const char* who) {
+                   unsigned long long record_bytes, const char* who) {
   char msg[200];
   if (Q.x_dev == nullptr || Q.count_dev == nullptr || (Q.y_dev == nullptr && Q.n > 0) ||
       (Q.pos_dev == nullptr && Q.cap > 0) || !aligned8(Q.pos_dev) || !aligned8(Q.count_dev)) {
@@ -285,10 +294,10 @@ int plan_add_query(BatchPlan& plan, const hc_batch_query& Q, size_t i, const Que
   plan.lay.ring_bytes = std::max(plan.lay.ring_bytes, static_cast<uint32_t>(a.stages) * a.stage_bytes);
   a.nwin = Q.n - Q.m + 1;
   a.num_chunks = (a.nwin + a.C - 1) / a.C;
-  a.chunks_per_cta = std::max<unsigned long long>(1, (kTileTextBytes + a.C - 1) / a.C);
+  a.chunks_per_cta = std::max<unsigned long long>(1, std::min(record_bytes, kTileTextBytes) / a.C);
   a.records = (a.num_chunks + a.chunks_per_cta - 1) / a.chunks_per_cta;
   const unsigned long long spill =
-      a.cap == 0 ? 0 : std::min<unsigned long long>(a.nwin, std::max<unsigned long long>(a.cap, 4096));
+      a.cap == 0 ? 0 : std::min<unsigned long long>(a.nwin, std::max<unsigned long long>(a.cap, kMinSpill));
   a.region_entries = (std::max<unsigned long long>(1, (spill + a.records - 1) / a.records) + 3) & ~3ull;
   plan.ws_bytes += a.records * 16 + a.records * a.region_entries * 4;
   const unsigned long long groups = (a.records + 15) / 16;
@@ -487,6 +496,9 @@ int create_batch(const hc_batch_query* qs, size_t nq, const hc_tuner* tuner, hc_
   if (b == nullptr) return set_error(HC_ERR_NOMEM, std::string(who) + ": out of host memory");
   BatchPlan& plan = b->plan;
   plan.args.reserve(nq);
+  unsigned long long total_text = 0;
+  for (size_t i = 0; i < nq; ++i) total_text += qs[i].n;
+  const unsigned long long rec_bytes = record_bytes_for(total_text, dev);
   size_t k = 0;
   for (size_t i = 0; i < nq; ++i) {
     const hc_batch_query& Q = qs[i];
@@ -505,7 +517,7 @@ int create_batch(const hc_batch_query* qs, size_t nq, const hc_tuner* tuner, hc_
     } else {
       p.q = Q.q;  // negative: rejected below
     }
-    int rc = plan_add_query(plan, Q, i, p, who);
+    int rc = plan_add_query(plan, Q, i, p, rec_bytes, who);
     if (rc != HC_OK) {
       delete b;
       return rc;

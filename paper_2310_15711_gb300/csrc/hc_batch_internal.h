@@ -55,10 +55,16 @@ struct BatchPlan {
   size_t smem_pre = 0, smem_scan = 0, smem_emit = 0;
 };
 
-// Appends query Q (index i, for messages) with parameters p to the plan.
+// Text bytes per record (one warp's share of a query) for a batch of
+// `total_text` bytes on device dev: enough records to give every warp slot
+// of the GPU (SMs x 16) work when the batch is small, at most 64 KiB each.
+unsigned long long record_bytes_for(unsigned long long total_text, int dev);
+
+// Appends query Q (index i, for messages) with parameters p to the plan, its
+// text cut into records of about record_bytes (whole chunks, at least one).
 // Checks pointers, alignment and parameter ranges; reads no device memory.
 int plan_add_query(BatchPlan& plan, const hc_batch_query& Q, size_t i, const QueryParams& p,
-                   const char* who);
+                   unsigned long long record_bytes, const char* who);
 // Shared-memory layout of the plan; HC_ERR_ARG when the largest query's
 // filter and staging buffers do not fit in one CTA.
 int plan_finish(BatchPlan& plan, int dev, const char* who);

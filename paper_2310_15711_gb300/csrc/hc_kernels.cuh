@@ -590,21 +590,32 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
         unsigned long long out = P + stored;
         Sink cs_sink{};
         cs_sink.slot = slots + tid;
-        for (unsigned long long c = c0 + (ovf >> 40); c < c1 && out < a.cap; ++c) {
+        // a chunk is C / L lane segments of L window starts (32 for the
+        // per-warp chunks, kThreads for the dense ones): the CTA re-scans
+        // kThreads * L / C consecutive chunks per round, thread order =
+        // chunk-major, so the block scan keeps positions ascending
+        const int lanes = static_cast<int>(a.C / static_cast<uint32_t>(a.L));
+        const int per_round = max(1, kThreads / lanes);
+        const int sub = tid / lanes;
+        const int lo = (tid % lanes) * a.L;
+        for (unsigned long long cb = c0 + (ovf >> 40); cb < c1 && out < a.cap; cb += per_round) {
+          const unsigned long long c = cb + static_cast<unsigned long long>(sub);
+          const bool mine = sub < per_round && c < c1;
           const unsigned long long cs = c * a.C;
-          const int wins = static_cast<int>(min(static_cast<unsigned long long>(a.C), a.nwin - cs));
-          const int lo = tid * a.L;
-          const int hi = max(lo, min(lo + a.L, wins));
-          const uint8_t* base = a.y + cs;
-          const int cnt = scan_segment<Q, false, kCount>(base, 0, lo, hi, a, Fs, a.x, cs_sink);
+          int hi = lo;
+          if (mine) hi = max(lo, min(lo + a.L, static_cast<int>(min(static_cast<unsigned long long>(a.C), a.nwin - cs))));
+          const uint8_t* base = a.y + (mine ? cs : 0ull);
+          const int cnt = mine ? scan_segment<Q, false, kCount>(base, 0, lo, hi, a, Fs, a.x, cs_sink) : 0;
           uint32_t excl, total;
           block_scan(static_cast<uint32_t>(cnt), warp_sum, &excl, &total);
-          Sink w{};
-          w.pos = a.pos;
-          w.obase = out + excl;
-          w.vbase = cs;
-          w.limit = a.cap;
-          scan_segment<Q, false, kToPositions>(base, 0, lo, cnt > 0 ? hi : lo, a, Fs, a.x, w);
+          if (mine) {  // warp-uniform: scan_segment is called by whole warps
+            Sink w{};
+            w.pos = a.pos;
+            w.obase = out + excl;
+            w.vbase = cs;
+            w.limit = a.cap;
+            scan_segment<Q, false, kToPositions>(base, 0, lo, cnt > 0 ? hi : lo, a, Fs, a.x, w);
+          }
           out += total;
           __syncthreads();
         }

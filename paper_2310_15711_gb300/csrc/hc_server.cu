@@ -68,9 +68,9 @@ struct Req {
   std::vector<uint8_t> x;
   QueryParams p;
   uint64_t cap = 0;
-  // sizes of the request's share of a batch (from its one-query plan)
+  // shared-memory layout and admitted device bytes (an estimate from its
+  // one-query plan; the batch it joins is planned again at launch)
   BatchLayout lay{};
-  size_t filter_words = 0, ws_bytes = 0, ntiles = 0, netiles = 0;
   uint64_t dev_bytes = 0;
   // outcome
   uint64_t submit_ns = 0, start_ns = 0, done_ns = 0;
@@ -220,23 +220,6 @@ void Server::fail(std::vector<Req*>& b, int status) {
 // [counter | args | tiles | emit tiles | patterns | filters | workspace].
 int Server::launch(Slot& s, std::vector<Req*>& b) {
   const size_t nq = b.size();
-  size_t ntiles = 0, netiles = 0, xbytes = 0, fwords = 0, ws = 0;
-  for (Req* r : b) {
-    ntiles += r->ntiles;
-    netiles += r->netiles;
-    xbytes += align_up(r->x.size(), 16);
-    fwords += r->filter_words;
-    ws += r->ws_bytes;
-  }
-  const size_t o_args = kAlign;
-  const size_t o_tiles = o_args + align_up(nq * sizeof(SearchArgs));
-  const size_t o_etiles = o_tiles + align_up(ntiles * sizeof(BatchTile));
-  const size_t o_x = o_etiles + align_up(netiles * sizeof(EmitTile));
-  const size_t table_end = o_x + align_up(xbytes);
-  const size_t o_f = table_end;
-  const size_t o_ws = o_f + align_up(fwords * 4);
-  const size_t total = o_ws + align_up(ws);
-
   // result arena: counts, then each request's positions
   s.pos_off.assign(nq, 0);
   size_t entries = nq;
@@ -257,20 +240,21 @@ int Server::launch(Slot& s, std::vector<Req*>& b) {
   if (cfg.plain) {
     rc = launch_plain(s, b);
   } else {
-    rc = grow_pinned(&s.stage, &s.stage_cap, table_end, cudaHostAllocPortable, "cudaHostAlloc(server staging)");
-    if (rc != HC_OK) return rc;
-    void* blk = nullptr;
-    e = cudaMallocFromPoolAsync(&blk, total, device_pool(dev), s.stream);
-    if (e != cudaSuccess) return cuda_error(e, "cudaMallocFromPoolAsync(server batch)");
-    uint8_t* d = static_cast<uint8_t*>(blk);
+    // plan first (patterns at placeholder addresses, patched below), then
+    // one device block sized from the plan:
+    // [counter | args | tiles | emit tiles | patterns | filters | workspace]
+    static const uint64_t placeholder[2] = {0, 0};
     BatchPlan plan;
     plan.args.reserve(nq);
-    size_t xo = 0;
+    unsigned long long total_text = 0;
+    for (Req* r : b) total_text += r->n;
+    const unsigned long long rec_bytes = record_bytes_for(total_text, dev);
+    std::vector<size_t> xoff(nq);
+    size_t xbytes = 0;
     for (size_t i = 0; i < nq && rc == HC_OK; ++i) {
       Req* r = b[i];
-      std::memcpy(s.stage + o_x + xo, r->x.data(), r->x.size());
       hc_batch_query Q{};
-      Q.x_dev = d + o_x + xo;
+      Q.x_dev = reinterpret_cast<const uint8_t*>(placeholder);
       Q.m = r->x.size();
       Q.y_dev = r->y;
       Q.n = r->n;
@@ -281,22 +265,40 @@ int Server::launch(Slot& s, std::vector<Req*>& b) {
       Q.count_dev = reinterpret_cast<uint64_t*>(s.res_dev + i);
       Q.lane_bytes = r->p.lane_bytes;
       Q.mode = r->p.mode;
-      rc = plan_add_query(plan, Q, i, r->p, "hc_server");
-      xo += align_up(r->x.size(), 16);
+      rc = plan_add_query(plan, Q, i, r->p, rec_bytes, "hc_server");
+      xoff[i] = xbytes;
+      xbytes += align_up(r->x.size(), 16);
     }
     if (rc == HC_OK) rc = plan_finish(plan, dev, "hc_server");
     BatchLaunch L;
     if (rc == HC_OK) rc = batch_grid(plan, dev, &L.grid_scan);
-    if (rc == HC_OK) {
-      plan_bind(plan, reinterpret_cast<uint32_t*>(d + o_f), d + o_ws);
-      std::memcpy(s.stage + o_args, plan.args.data(), nq * sizeof(SearchArgs));
-      if (!plan.tiles.empty())
-        std::memcpy(s.stage + o_tiles, plan.tiles.data(), plan.tiles.size() * sizeof(BatchTile));
-      if (!plan.etiles.empty())
-        std::memcpy(s.stage + o_etiles, plan.etiles.data(), plan.etiles.size() * sizeof(EmitTile));
-      e = cudaMemcpyAsync(d + o_args, s.stage + o_args, table_end - o_args, cudaMemcpyHostToDevice, s.stream);
-      if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpyAsync(server tables)");
+    if (rc != HC_OK) return rc;
+    const size_t o_args = kAlign;
+    const size_t o_tiles = o_args + align_up(nq * sizeof(SearchArgs));
+    const size_t o_etiles = o_tiles + align_up(plan.tiles.size() * sizeof(BatchTile));
+    const size_t o_x = o_etiles + align_up(plan.etiles.size() * sizeof(EmitTile));
+    const size_t table_end = o_x + align_up(xbytes);
+    const size_t o_f = table_end;
+    const size_t o_ws = o_f + align_up(plan.filter_words * 4);
+    const size_t total = o_ws + align_up(plan.ws_bytes);
+    rc = grow_pinned(&s.stage, &s.stage_cap, table_end, cudaHostAllocPortable, "cudaHostAlloc(server staging)");
+    if (rc != HC_OK) return rc;
+    void* blk = nullptr;
+    e = cudaMallocFromPoolAsync(&blk, total, device_pool(dev), s.stream);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMallocFromPoolAsync(server batch)");
+    uint8_t* d = static_cast<uint8_t*>(blk);
+    plan_bind(plan, reinterpret_cast<uint32_t*>(d + o_f), d + o_ws);
+    for (size_t i = 0; i < nq; ++i) {
+      std::memcpy(s.stage + o_x + xoff[i], b[i]->x.data(), b[i]->x.size());
+      plan.args[i].x = d + o_x + xoff[i];
     }
+    std::memcpy(s.stage + o_args, plan.args.data(), nq * sizeof(SearchArgs));
+    if (!plan.tiles.empty())
+      std::memcpy(s.stage + o_tiles, plan.tiles.data(), plan.tiles.size() * sizeof(BatchTile));
+    if (!plan.etiles.empty())
+      std::memcpy(s.stage + o_etiles, plan.etiles.data(), plan.etiles.size() * sizeof(EmitTile));
+    e = cudaMemcpyAsync(d + o_args, s.stage + o_args, table_end - o_args, cudaMemcpyHostToDevice, s.stream);
+    if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpyAsync(server tables)");
     if (rc == HC_OK) {
       L.args = reinterpret_cast<const SearchArgs*>(d + o_args);
       L.tiles = reinterpret_cast<const BatchTile*>(d + o_tiles);
@@ -687,20 +689,17 @@ int make_request(Server* s, const hc_server_request& q, uint64_t submit_ns, Req*
   Q.cap = r->cap;
   Q.count_dev = const_cast<uint64_t*>(placeholder);
   BatchPlan plan;
-  int rc = plan_add_query(plan, Q, 0, r->p, "hc_server_submit");
+  // sized as a batch of its own (the finest records it can be given)
+  int rc = plan_add_query(plan, Q, 0, r->p, record_bytes_for(t.n, s->dev), "hc_server_submit");
   if (rc == HC_OK) rc = plan_finish(plan, s->dev, "hc_server_submit");
   if (rc != HC_OK) {
     delete r;
     return rc;
   }
   r->lay = plan.lay;
-  r->filter_words = plan.filter_words;
-  r->ws_bytes = plan.ws_bytes;
-  r->ntiles = plan.tiles.size();
-  r->netiles = plan.etiles.size();
-  r->dev_bytes = align_up(sizeof(SearchArgs)) + align_up(r->ntiles * sizeof(BatchTile)) +
-                 align_up(r->netiles * sizeof(EmitTile)) + align_up(q.m, 16) + align_up(r->filter_words * 4) +
-                 align_up(r->ws_bytes);
+  r->dev_bytes = align_up(sizeof(SearchArgs)) + align_up(plan.tiles.size() * sizeof(BatchTile)) +
+                 align_up(plan.etiles.size() * sizeof(EmitTile)) + align_up(q.m, 16) +
+                 align_up(plan.filter_words * 4) + align_up(plan.ws_bytes);
   r->submit_ns = submit_ns;
   *out = r;
   return HC_OK;

@@ -164,7 +164,7 @@ int time_candidate(Scratch& sc, int dev, const uint8_t* x, uint64_t m, const uin
   Q.lane_bytes = p.lane_bytes;
   Q.mode = p.mode;
   BatchPlan plan;
-  if (plan_add_query(plan, Q, 0, p, "hc_tuner_calibrate") != HC_OK ||
+  if (plan_add_query(plan, Q, 0, p, record_bytes_for(n, dev), "hc_tuner_calibrate") != HC_OK ||
       plan_finish(plan, dev, "hc_tuner_calibrate") != HC_OK) {
     clear_error();  // does not fit: skipped
     return HC_OK;
