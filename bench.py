@@ -65,6 +65,8 @@ def parse_args():
                          "request streams into the server vs. a plain per-request server")
     ap.add_argument("--served-rates", type=int, nargs="+", default=list(SERVED_RATES_DEFAULT))
     ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-backlog", type=int, default=50000,
+                    help="requests submitted at once for the saturation measurement")
     ap.add_argument("--batch-queries", type=int, default=4096)
     ap.add_argument("--tune-text-bytes", type=int, default=256 << 20,
                     help="calibration text per alphabet size (batched workload)")
@@ -608,6 +610,36 @@ def run_served(args, rank, world, local_rank):
         entry["p99_ratio_plain_over_batched"] = round(
             entry["plain"]["p99_us"] / max(entry["batched"]["p99_us"], 1e-9), 3)
         loads.append(entry)
+    # saturation: a backlog of requests submitted at once, drained as fast as
+    # each server can (capacity in requests/s and text GB/s)
+    sat = {}
+    nsat = args.served_backlog
+    stream = hi.served_requests(texts, nsat, 1e9, seed=99)
+    sat_counts = {}
+    for plain in (0, 1):
+        srv = hc.HCServer(hc.ServerConfig(plain=plain), tuner)
+        tids = [srv.add_text(y, sigma=texts[i][1]) for i, y in enumerate(ydev)]
+        rq = [(tids[ti], yhost[ti][off:off + m]) for _, ti, m, off in stream]
+        srv.replay(rq[:500], [0.0] * min(500, len(rq)))
+        srv.drain()
+        while srv.poll(65536, positions=False):
+            pass
+        ids = srv.replay(rq, [0.0] * len(rq))
+        srv.drain()
+        res = []
+        while len(res) < nsat:
+            res += srv.poll(65536, wait_us=100_000, positions=False)
+        srv.destroy()
+        pos = {rid: k for k, rid in enumerate(ids)}
+        span = (max(r["done_ns"] for r in res) - min(r["submit_ns"] for r in res)) / 1e9
+        nbytes = sum(texts[stream[pos[r["id"]]][1]][0] for r in res)
+        sat_counts[plain] = {pos[r["id"]]: r["count"] for r in res}
+        sat["plain" if plain else "batched"] = {
+            "req_per_s": round(nsat / span, 1), "GBps": round(nbytes / span / GB, 3),
+            "mean_batch": round(nsat / max(len({r["batch"] for r in res}), 1), 2)}
+    sat["requests"] = nsat
+    sat["speedup_vs_plain"] = round(sat["batched"]["req_per_s"] / sat["plain"]["req_per_s"], 3)
+    sat["counts_equal"] = sat_counts[0] == sat_counts[1]
     top = loads[-1]
     line = {
         "metric": "served HC: aggregate text GB/s at the highest offered load (p50/p99 latency per load)",
@@ -622,7 +654,7 @@ def run_served(args, rank, world, local_rank):
                    "admission_GiB": 32, "q_alpha": "autotuned (sigma in {4, 20, 95}, m 2 .. 1024)",
                    "latency": "scheduled arrival -> result copied on the host"},
         "p50_us": top["batched"]["p50_us"], "p99_us": top["batched"]["p99_us"],
-        "loads": loads, "tune_s": round(tune_s, 2),
+        "loads": loads, "saturation": sat, "tune_s": round(tune_s, 2),
     }
     print(json.dumps(line), flush=True)
     tuner.free()

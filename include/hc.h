@@ -316,7 +316,8 @@ void hc_tuner_free(hc_tuner *t);
  * no copy step follows a batch.
  *
  * plain = 1 runs each request as one plain search launch (host-built filter,
- * the kernels of hc_search_async) instead: the comparison form.
+ * the kernels of hc_search_async) instead: the comparison form.  A batch
+ * that holds one request runs that way too unless no_solo_plain = 1.
  */
 typedef struct hc_server hc_server;
 
@@ -327,7 +328,8 @@ typedef struct hc_server_config {
     int max_batch;          /* requests per batch, 1..2^20; 0 = 1024 */
     uint64_t default_cap;   /* positions kept per request when its cap is 0; 0 = 4096 */
     int plain;              /* 1: one plain search launch per request */
-    int reserved;
+    int no_solo_plain;      /* 1: a batch of one request also runs the batched
+                               kernels (0: it runs the single-search kernels) */
 } hc_server_config;
 
 typedef struct hc_server_request {

@@ -24,6 +24,8 @@
 // Plain mode (comparison): each request is preprocessed on the host and runs
 // as one plain search launch (scan and emit kernels of hc_search_async), the
 // requests of one assembly still sharing one stream and one completion event.
+// A batch that holds a single request runs that way too (its kernels are
+// the ones tuned for one query), unless the configuration asks otherwise.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -237,8 +239,8 @@ int Server::launch(Slot& s, std::vector<Req*>& b) {
   }
   if (rc != HC_OK) return rc;
   cudaError_t e;
-  if (cfg.plain) {
-    rc = launch_plain(s, b);
+  if (cfg.plain || (b.size() == 1 && !cfg.no_solo_plain)) {
+    rc = launch_plain(s, b);  // a lone request runs the single-search kernels
   } else {
     // plan first (patterns at placeholder addresses, patched below), then
     // one device block sized from the plan:

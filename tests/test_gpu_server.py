@@ -76,8 +76,11 @@ def _collect(srv, n):
     return got
 
 
-def test_alone_equals_in_the_mix(hc):
-    srv = hc.HCServer()
+@pytest.mark.parametrize("no_solo_plain", [0, 1])
+def test_alone_equals_in_the_mix(hc, no_solo_plain):
+    """Alone, the probe runs as a batch of one (single-search kernels, or the
+    batched kernels with no_solo_plain); in the mix it shares batches."""
+    srv = hc.HCServer(hc.ServerConfig(no_solo_plain=no_solo_plain))
     ys, ids = _texts(srv)
     rng = np.random.default_rng(1)
     probe_t = 2
