@@ -316,8 +316,9 @@ void hc_tuner_free(hc_tuner *t);
  * no copy step follows a batch.
  *
  * plain = 1 runs each request as one plain search launch (host-built filter,
- * the kernels of hc_search_async) instead: the comparison form.  A batch
- * that holds one request runs that way too unless no_solo_plain = 1.
+ * the kernels of hc_search_async) instead: the comparison form.  Otherwise
+ * requests with m = q (served best by the dense single-search kernel) and
+ * a batch's lone request run that way too, unless batch_only = 1.
  */
 typedef struct hc_server hc_server;
 
@@ -328,8 +329,9 @@ typedef struct hc_server_config {
     int max_batch;          /* requests per batch, 1..2^20; 0 = 1024 */
     uint64_t default_cap;   /* positions kept per request when its cap is 0; 0 = 4096 */
     int plain;              /* 1: one plain search launch per request */
-    int no_solo_plain;      /* 1: a batch of one request also runs the batched
-                               kernels (0: it runs the single-search kernels) */
+    int batch_only;         /* 1: every request runs the batched kernels (0:
+                               requests with m = q and a batch's lone request
+                               run the single-search kernels) */
 } hc_server_config;
 
 typedef struct hc_server_request {

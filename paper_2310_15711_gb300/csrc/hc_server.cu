@@ -24,8 +24,9 @@
 // Plain mode (comparison): each request is preprocessed on the host and runs
 // as one plain search launch (scan and emit kernels of hc_search_async), the
 // requests of one assembly still sharing one stream and one completion event.
-// A batch that holds a single request runs that way too (its kernels are
-// the ones tuned for one query), unless the configuration asks otherwise.
+// In the batched mode the same single-search launches serve the requests
+// with m = q (the dense single-search kernel, one q-gram per window) and a
+// batch's lone request, unless batch_only is set.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -89,8 +90,10 @@ struct Slot {
   bool busy = false;
   std::vector<Req*> reqs;
   std::vector<size_t> pos_off;  // per request: first entry of its positions in the result arena
-  uint8_t* stage = nullptr;     // pinned host staging of the launch tables
+  uint8_t* stage = nullptr;     // pinned host staging of the batched launch tables
   size_t stage_cap = 0;
+  uint8_t* stage_plain = nullptr;  // ... and of the single-search filters (a separate
+  size_t stage_plain_cap = 0;      // buffer: both copies may be in flight at once)
   uint8_t* res = nullptr;       // mapped pinned host memory: counts, then positions
   uint64_t* res_dev = nullptr;  // its device address
   size_t res_cap = 0;           // bytes
@@ -129,7 +132,8 @@ struct Server {
   void run();
   std::vector<Req*> take_batch();
   int launch(Slot& s, std::vector<Req*>& b);
-  int launch_plain(Slot& s, std::vector<Req*>& b);
+  int launch_batched(Slot& s, const std::vector<size_t>& which);
+  int launch_plain(Slot& s, const std::vector<size_t>& which);
   void finish(Slot& s, cudaError_t q);
   void fail(std::vector<Req*>& b, int status);
 };
@@ -238,85 +242,22 @@ int Server::launch(Slot& s, std::vector<Req*>& b) {
     s.res_dev = static_cast<uint64_t*>(d);
   }
   if (rc != HC_OK) return rc;
-  cudaError_t e;
-  if (cfg.plain || (b.size() == 1 && !cfg.no_solo_plain)) {
-    rc = launch_plain(s, b);  // a lone request runs the single-search kernels
-  } else {
-    // plan first (patterns at placeholder addresses, patched below), then
-    // one device block sized from the plan:
-    // [counter | args | tiles | emit tiles | patterns | filters | workspace]
-    static const uint64_t placeholder[2] = {0, 0};
-    BatchPlan plan;
-    plan.args.reserve(nq);
-    unsigned long long total_text = 0;
-    for (Req* r : b) total_text += r->n;
-    const unsigned long long rec_bytes = record_bytes_for(total_text, dev);
-    std::vector<size_t> xoff(nq);
-    size_t xbytes = 0;
-    for (size_t i = 0; i < nq && rc == HC_OK; ++i) {
-      Req* r = b[i];
-      hc_batch_query Q{};
-      Q.x_dev = reinterpret_cast<const uint8_t*>(placeholder);
-      Q.m = r->x.size();
-      Q.y_dev = r->y;
-      Q.n = r->n;
-      Q.q = r->p.q;
-      Q.alpha = r->p.alpha;
-      Q.pos_dev = r->cap ? reinterpret_cast<uint64_t*>(s.res_dev + s.pos_off[i]) : nullptr;
-      Q.cap = r->cap;
-      Q.count_dev = reinterpret_cast<uint64_t*>(s.res_dev + i);
-      Q.lane_bytes = r->p.lane_bytes;
-      Q.mode = r->p.mode;
-      rc = plan_add_query(plan, Q, i, r->p, rec_bytes, "hc_server");
-      xoff[i] = xbytes;
-      xbytes += align_up(r->x.size(), 16);
-    }
-    if (rc == HC_OK) rc = plan_finish(plan, dev, "hc_server");
-    BatchLaunch L;
-    if (rc == HC_OK) rc = batch_grid(plan, dev, &L.grid_scan);
-    if (rc != HC_OK) return rc;
-    const size_t o_args = kAlign;
-    const size_t o_tiles = o_args + align_up(nq * sizeof(SearchArgs));
-    const size_t o_etiles = o_tiles + align_up(plan.tiles.size() * sizeof(BatchTile));
-    const size_t o_x = o_etiles + align_up(plan.etiles.size() * sizeof(EmitTile));
-    const size_t table_end = o_x + align_up(xbytes);
-    const size_t o_f = table_end;
-    const size_t o_ws = o_f + align_up(plan.filter_words * 4);
-    const size_t total = o_ws + align_up(plan.ws_bytes);
-    rc = grow_pinned(&s.stage, &s.stage_cap, table_end, cudaHostAllocPortable, "cudaHostAlloc(server staging)");
-    if (rc != HC_OK) return rc;
-    void* blk = nullptr;
-    e = cudaMallocFromPoolAsync(&blk, total, device_pool(dev), s.stream);
-    if (e != cudaSuccess) return cuda_error(e, "cudaMallocFromPoolAsync(server batch)");
-    uint8_t* d = static_cast<uint8_t*>(blk);
-    plan_bind(plan, reinterpret_cast<uint32_t*>(d + o_f), d + o_ws);
-    for (size_t i = 0; i < nq; ++i) {
-      std::memcpy(s.stage + o_x + xoff[i], b[i]->x.data(), b[i]->x.size());
-      plan.args[i].x = d + o_x + xoff[i];
-    }
-    std::memcpy(s.stage + o_args, plan.args.data(), nq * sizeof(SearchArgs));
-    if (!plan.tiles.empty())
-      std::memcpy(s.stage + o_tiles, plan.tiles.data(), plan.tiles.size() * sizeof(BatchTile));
-    if (!plan.etiles.empty())
-      std::memcpy(s.stage + o_etiles, plan.etiles.data(), plan.etiles.size() * sizeof(EmitTile));
-    e = cudaMemcpyAsync(d + o_args, s.stage + o_args, table_end - o_args, cudaMemcpyHostToDevice, s.stream);
-    if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpyAsync(server tables)");
-    if (rc == HC_OK) {
-      L.args = reinterpret_cast<const SearchArgs*>(d + o_args);
-      L.tiles = reinterpret_cast<const BatchTile*>(d + o_tiles);
-      L.etiles = reinterpret_cast<const EmitTile*>(d + o_etiles);
-      L.counter = reinterpret_cast<unsigned long long*>(d);
-      L.nq = nq;
-      L.ntiles = plan.tiles.size();
-      L.netiles = plan.etiles.size();
-      L.lay = plan.lay;
-      L.smem_pre = plan.smem_pre;
-      L.smem_scan = plan.smem_scan;
-      L.smem_emit = plan.smem_emit;
-      rc = launch_batch(L, s.stream);
-    }
-    cudaFreeAsync(blk, s.stream);  // after the kernels, in stream order
+  // routing: m = q requests (one q-gram per window: the dense single-search
+  // kernel) and a batch's lone request run the single-search kernels; the
+  // rest run the batched kernels
+  std::vector<size_t> solo, batched;
+  for (size_t i = 0; i < nq; ++i) {
+    const bool dense = b[i]->x.size() == static_cast<size_t>(b[i]->p.q);
+    if (cfg.plain || (!cfg.batch_only && dense)) solo.push_back(i);
+    else batched.push_back(i);
   }
+  if (!cfg.batch_only && batched.size() == 1) {
+    solo.push_back(batched[0]);
+    batched.clear();
+  }
+  if (!batched.empty()) rc = launch_batched(s, batched);
+  if (rc == HC_OK && !solo.empty()) rc = launch_plain(s, solo);
+  cudaError_t e;
   if (rc == HC_OK) {
     e = cudaMemcpyAsync(s.status, status_word(), sizeof(unsigned int), cudaMemcpyDeviceToHost, s.stream);
     if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpyAsync(server status)");
@@ -327,42 +268,127 @@ int Server::launch(Slot& s, std::vector<Req*>& b) {
   return HC_OK;
 }
 
+// The batched kernels over requests `which` of the slot (indices into its
+// requests and result arena).
+int Server::launch_batched(Slot& s, const std::vector<size_t>& which) {
+  const size_t nq = which.size();
+  int rc = HC_OK;
+  cudaError_t e;
+  // plan first (patterns at placeholder addresses, patched below), then
+  // one device block sized from the plan:
+  // [counter | args | tiles | emit tiles | patterns | filters | workspace]
+  static const uint64_t placeholder[2] = {0, 0};
+  BatchPlan plan;
+  plan.args.reserve(nq);
+  unsigned long long total_text = 0;
+  for (size_t w : which) total_text += s.reqs[w]->n;
+  const unsigned long long rec_bytes = record_bytes_for(total_text, dev);
+  std::vector<size_t> xoff(nq);
+  size_t xbytes = 0;
+  for (size_t i = 0; i < nq && rc == HC_OK; ++i) {
+    Req* r = s.reqs[which[i]];
+    hc_batch_query Q{};
+    Q.x_dev = reinterpret_cast<const uint8_t*>(placeholder);
+    Q.m = r->x.size();
+    Q.y_dev = r->y;
+    Q.n = r->n;
+    Q.q = r->p.q;
+    Q.alpha = r->p.alpha;
+    Q.pos_dev = r->cap ? reinterpret_cast<uint64_t*>(s.res_dev + s.pos_off[which[i]]) : nullptr;
+    Q.cap = r->cap;
+    Q.count_dev = reinterpret_cast<uint64_t*>(s.res_dev + which[i]);
+    Q.lane_bytes = r->p.lane_bytes;
+    Q.mode = r->p.mode;
+    rc = plan_add_query(plan, Q, i, r->p, rec_bytes, "hc_server");
+    xoff[i] = xbytes;
+    xbytes += align_up(r->x.size(), 16);
+  }
+  if (rc == HC_OK) rc = plan_finish(plan, dev, "hc_server");
+  BatchLaunch L;
+  if (rc == HC_OK) rc = batch_grid(plan, dev, &L.grid_scan);
+  if (rc != HC_OK) return rc;
+  const size_t o_args = kAlign;
+  const size_t o_tiles = o_args + align_up(nq * sizeof(SearchArgs));
+  const size_t o_etiles = o_tiles + align_up(plan.tiles.size() * sizeof(BatchTile));
+  const size_t o_x = o_etiles + align_up(plan.etiles.size() * sizeof(EmitTile));
+  const size_t table_end = o_x + align_up(xbytes);
+  const size_t o_f = table_end;
+  const size_t o_ws = o_f + align_up(plan.filter_words * 4);
+  const size_t total = o_ws + align_up(plan.ws_bytes);
+  rc = grow_pinned(&s.stage, &s.stage_cap, table_end, cudaHostAllocPortable, "cudaHostAlloc(server staging)");
+  if (rc != HC_OK) return rc;
+  void* blk = nullptr;
+  e = cudaMallocFromPoolAsync(&blk, total, device_pool(dev), s.stream);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMallocFromPoolAsync(server batch)");
+  uint8_t* d = static_cast<uint8_t*>(blk);
+  plan_bind(plan, reinterpret_cast<uint32_t*>(d + o_f), d + o_ws);
+  for (size_t i = 0; i < nq; ++i) {
+    std::memcpy(s.stage + o_x + xoff[i], s.reqs[which[i]]->x.data(), s.reqs[which[i]]->x.size());
+    plan.args[i].x = d + o_x + xoff[i];
+  }
+  std::memcpy(s.stage + o_args, plan.args.data(), nq * sizeof(SearchArgs));
+  if (!plan.tiles.empty())
+    std::memcpy(s.stage + o_tiles, plan.tiles.data(), plan.tiles.size() * sizeof(BatchTile));
+  if (!plan.etiles.empty())
+    std::memcpy(s.stage + o_etiles, plan.etiles.data(), plan.etiles.size() * sizeof(EmitTile));
+  e = cudaMemcpyAsync(d + o_args, s.stage + o_args, table_end - o_args, cudaMemcpyHostToDevice, s.stream);
+  if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpyAsync(server tables)");
+  if (rc == HC_OK) {
+    L.args = reinterpret_cast<const SearchArgs*>(d + o_args);
+    L.tiles = reinterpret_cast<const BatchTile*>(d + o_tiles);
+    L.etiles = reinterpret_cast<const EmitTile*>(d + o_etiles);
+    L.counter = reinterpret_cast<unsigned long long*>(d);
+    L.nq = nq;
+    L.ntiles = plan.tiles.size();
+    L.netiles = plan.etiles.size();
+    L.lay = plan.lay;
+    L.smem_pre = plan.smem_pre;
+    L.smem_scan = plan.smem_scan;
+    L.smem_emit = plan.smem_emit;
+    rc = launch_batch(L, s.stream);
+  }
+  cudaFreeAsync(blk, s.stream);  // after the kernels, in stream order
+  return rc;
+}
+
 // Plain mode: per request a host-built filter (hc_preprocess), uploaded with
 // the others in one copy, and one plain search launch with its own
 // stream-ordered workspace.
-int Server::launch_plain(Slot& s, std::vector<Req*>& b) {
-  std::vector<hc_filter*> fs(b.size(), nullptr);
+int Server::launch_plain(Slot& s, const std::vector<size_t>& which) {
+  const size_t nq = which.size();
+  std::vector<hc_filter*> fs(nq, nullptr);
   size_t off = 0;
   int rc = HC_OK;
-  std::vector<size_t> offs(b.size());
-  for (size_t i = 0; i < b.size() && rc == HC_OK; ++i) {
-    Req* r = b[i];
+  std::vector<size_t> offs(nq);
+  for (size_t i = 0; i < nq && rc == HC_OK; ++i) {
+    Req* r = s.reqs[which[i]];
     rc = hc_preprocess(r->x.data(), r->x.size(), r->p.q, r->p.alpha, &fs[i]);
     if (rc != HC_OK) break;
     const Filter* f = as_filter(fs[i]);
     offs[i] = off;
     off += align_up(f->F.size() * 4 + r->x.size(), 16);
   }
-  if (rc == HC_OK) rc = grow_pinned(&s.stage, &s.stage_cap, off, cudaHostAllocPortable, "cudaHostAlloc(server staging)");
+  if (rc == HC_OK)
+    rc = grow_pinned(&s.stage_plain, &s.stage_plain_cap, off, cudaHostAllocPortable, "cudaHostAlloc(server staging)");
   void* fx = nullptr;
   if (rc == HC_OK) {
     cudaError_t e = cudaMallocFromPoolAsync(&fx, std::max<size_t>(off, 16), device_pool(dev), s.stream);
     if (e != cudaSuccess) rc = cuda_error(e, "cudaMallocFromPoolAsync(server plain filters)");
   }
   if (rc == HC_OK) {
-    for (size_t i = 0; i < b.size(); ++i) {
+    for (size_t i = 0; i < nq; ++i) {
       const Filter* f = as_filter(fs[i]);
-      std::memcpy(s.stage + offs[i], f->F.data(), f->F.size() * 4);
-      std::memcpy(s.stage + offs[i] + f->F.size() * 4, b[i]->x.data(), b[i]->x.size());
+      std::memcpy(s.stage_plain + offs[i], f->F.data(), f->F.size() * 4);
+      std::memcpy(s.stage_plain + offs[i] + f->F.size() * 4, f->x.data(), f->x.size());
     }
-    cudaError_t e = cudaMemcpyAsync(fx, s.stage, off, cudaMemcpyHostToDevice, s.stream);
+    cudaError_t e = cudaMemcpyAsync(fx, s.stage_plain, off, cudaMemcpyHostToDevice, s.stream);
     if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpyAsync(server plain filters)");
   }
-  for (size_t i = 0; i < b.size() && rc == HC_OK; ++i) {
-    Req* r = b[i];
+  for (size_t i = 0; i < nq && rc == HC_OK; ++i) {
+    Req* r = s.reqs[which[i]];
     const Filter* f = as_filter(fs[i]);
-    uint64_t* count = reinterpret_cast<uint64_t*>(s.res_dev + i);
-    uint64_t* pos = r->cap ? reinterpret_cast<uint64_t*>(s.res_dev + s.pos_off[i]) : nullptr;
+    uint64_t* count = reinterpret_cast<uint64_t*>(s.res_dev + which[i]);
+    uint64_t* pos = r->cap ? reinterpret_cast<uint64_t*>(s.res_dev + s.pos_off[which[i]]) : nullptr;
     if (r->n < r->x.size()) {
       cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint64_t), s.stream);
       if (e != cudaSuccess) rc = cuda_error(e, "cudaMemsetAsync(server count)");
@@ -526,6 +552,7 @@ void destroy_server(Server* s) {
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.stream) cudaStreamDestroy(sl.stream);
     if (sl.stage) cudaFreeHost(sl.stage);
+    if (sl.stage_plain) cudaFreeHost(sl.stage_plain);
     if (sl.res) cudaFreeHost(sl.res);
     if (sl.status) cudaFreeHost(sl.status);
   }

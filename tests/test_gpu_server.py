@@ -76,11 +76,11 @@ def _collect(srv, n):
     return got
 
 
-@pytest.mark.parametrize("no_solo_plain", [0, 1])
-def test_alone_equals_in_the_mix(hc, no_solo_plain):
+@pytest.mark.parametrize("batch_only", [0, 1])
+def test_alone_equals_in_the_mix(hc, batch_only):
     """Alone, the probe runs as a batch of one (single-search kernels, or the
-    batched kernels with no_solo_plain); in the mix it shares batches."""
-    srv = hc.HCServer(hc.ServerConfig(no_solo_plain=no_solo_plain))
+    batched kernels with batch_only); in the mix it shares batches."""
+    srv = hc.HCServer(hc.ServerConfig(batch_only=batch_only))
     ys, ids = _texts(srv)
     rng = np.random.default_rng(1)
     probe_t = 2
