@@ -325,14 +325,10 @@ def run_gpu(args, rank, world, local_rank):
     cell_ms = np.array([sum(cell_ev[k][ci][0].elapsed_time(cell_ev[k][ci][1])
                             for k in range(args.steps)) for ci in range(ncell)])
 
-    t_local = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    step_ms_max = float(t_local.item())
-
     text_bytes_step = sum(texts[s].numel() * args.patterns for (s, m) in keys)
-    value = world * text_bytes_step * args.steps / (step_ms_max / 1e3) / GB
-    ms_per_step = step_ms_max / args.steps
+    step_s_max, job_bytes = combine_ranks(step_ms / 1e3, text_bytes_step * args.steps, dist, dev)
+    value = job_bytes / step_s_max / GB
+    ms_per_step = step_s_max * 1e3 / args.steps
 
     # algorithmic bytes per kernel family (per step): the scan kernels read
     # the text once and spill 4 bytes per occurrence; the emit kernel reads
@@ -377,7 +373,7 @@ def run_gpu(args, rank, world, local_rank):
 
     # ---- end to end through the synchronous C-ABI call, host buffers
     if not args.no_e2e:
-        line["e2e"] = e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream)
+        line["e2e"] = e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream, dist)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(texts_np, {k: v[0] for k, v in cells.items()},
                                             args.cpu_seconds, os.cpu_count() or 1)
@@ -660,7 +656,21 @@ def run_served(args, rank, world, local_rank):
     tuner.free()
 
 
-def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream):
+def combine_ranks(seconds, units, dist=None, device=None):
+    """Whole-job figures of a multi-rank run: the maximum of the ranks' times
+    and the sum of the units they processed (identity on one rank).  Every
+    rank must call it; with NCCL the tensors live on `device`."""
+    if dist is None:
+        return float(seconds), float(units)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream, dist=None):
     """One sweep step through hc_search (the synchronous C-ABI call): per
     sigma the text is copied from pinned host memory to the device, every
     pattern of every cell is searched, and each search's positions are read
@@ -673,6 +683,8 @@ def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream):
     h2d = d2h = 0
     text_bytes = 0
     torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for s in hi.SWEEP_SIGMAS:
@@ -691,7 +703,8 @@ def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream):
                     text_bytes += n
     stream.synchronize()
     dt = time.perf_counter() - t0
-    return {"value": round(text_bytes / dt / GB, 2), "unit": UNIT,
+    dt, total_bytes = combine_ranks(dt, text_bytes, dist, dev)
+    return {"value": round(total_bytes / dt / GB, 2), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "api": "hc_search (synchronous C-ABI call per pattern)"}
 
