@@ -317,8 +317,9 @@ void hc_tuner_free(hc_tuner *t);
  *
  * plain = 1 runs each request as one plain search launch (host-built filter,
  * the kernels of hc_search_async) instead: the comparison form.  Otherwise
- * requests with m = q (served best by the dense single-search kernel) and
- * a batch's lone request run that way too, unless batch_only = 1.
+ * a batch's lone request, and in batches of at most 16 the requests with
+ * m = q (served best by the dense single-search kernel), run that way too,
+ * unless batch_only = 1.
  */
 typedef struct hc_server hc_server;
 
@@ -330,8 +331,8 @@ typedef struct hc_server_config {
     uint64_t default_cap;   /* positions kept per request when its cap is 0; 0 = 4096 */
     int plain;              /* 1: one plain search launch per request */
     int batch_only;         /* 1: every request runs the batched kernels (0:
-                               requests with m = q and a batch's lone request
-                               run the single-search kernels) */
+                               a lone request, and m = q requests in batches
+                               of <= 16, run the single-search kernels) */
 } hc_server_config;
 
 typedef struct hc_server_request {

@@ -24,9 +24,9 @@
 // Plain mode (comparison): each request is preprocessed on the host and runs
 // as one plain search launch (scan and emit kernels of hc_search_async), the
 // requests of one assembly still sharing one stream and one completion event.
-// In the batched mode the same single-search launches serve the requests
-// with m = q (the dense single-search kernel, one q-gram per window) and a
-// batch's lone request, unless batch_only is set.
+// In the batched mode the same single-search launches serve a batch's lone
+// request and, in batches of at most 16, the requests with m = q (the dense
+// single-search kernel, one q-gram per window), unless batch_only is set.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -47,6 +47,7 @@ namespace {
 
 constexpr uint32_t kServerMagic = 0x48435356u;  // "HCSV"
 constexpr size_t kAlign = 256;
+constexpr size_t kSoloDenseMax = 16;  // batches up to this size route m = q requests to single searches
 
 size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
@@ -242,13 +243,16 @@ int Server::launch(Slot& s, std::vector<Req*>& b) {
     s.res_dev = static_cast<uint64_t*>(d);
   }
   if (rc != HC_OK) return rc;
-  // routing: m = q requests (one q-gram per window: the dense single-search
-  // kernel) and a batch's lone request run the single-search kernels; the
-  // rest run the batched kernels
+  // routing: in a small batch, m = q requests (one q-gram per window: the
+  // dense single-search kernel) run the single-search kernels, and so does a
+  // batch's lone request; the rest run the batched kernels.  In a large batch
+  // (a backlog) the per-launch host cost of the single searches would cost
+  // more than the dense kernel saves.
   std::vector<size_t> solo, batched;
+  const bool route_dense = !cfg.batch_only && nq <= kSoloDenseMax;
   for (size_t i = 0; i < nq; ++i) {
     const bool dense = b[i]->x.size() == static_cast<size_t>(b[i]->p.q);
-    if (cfg.plain || (!cfg.batch_only && dense)) solo.push_back(i);
+    if (cfg.plain || (route_dense && dense)) solo.push_back(i);
     else batched.push_back(i);
   }
   if (!cfg.batch_only && batched.size() == 1) {
