@@ -53,6 +53,7 @@ __device__ __forceinline__ uint32_t pattern_hash(const uint8_t* x, int i, int q,
 __global__ void __launch_bounds__(kThreads)
     hc_batch_preprocess_kernel(SearchArgs* args, unsigned long long* counter) {
   extern __shared__ __align__(128) uint8_t smem[];
+  pdl_launch_dependents();  // the scan kernel may be scheduled; it waits for this grid
   uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
   const int tid = threadIdx.x;
   if (blockIdx.x == 0 && tid == 0) *counter = 0;
@@ -115,6 +116,8 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
   __shared__ __align__(16) SearchArgs sa;
   __shared__ unsigned long long s_tile;
+  pdl_launch_dependents();
+  pdl_wait();  // filters, H_v and the work counter come from the preprocessing grid
   const int tid = threadIdx.x, warp = tid >> 5;
   uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
   uint8_t* xs = smem + lay.f_bytes;
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(kThreads)
     hc_batch_emit_kernel(const SearchArgs* args, const EmitTile* etiles) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(16) SearchArgs sa;
+  pdl_wait();  // the scan grid has completed and its records are visible
   const EmitTile et = etiles[blockIdx.x / kEmitSplit];
   const unsigned part = blockIdx.x % kEmitSplit;
   load_args(&sa, args + et.query);
@@ -369,15 +373,15 @@ int launch_batch(const BatchLaunch& L, cudaStream_t stream) {
     return HC_OK;
   }
   TimingToken t1 = timing_begin(kKindBatch, stream);
-  hc_batch_scan_kernel<<<L.grid_scan, kThreads, L.smem_scan, stream>>>(L.args, L.tiles, L.ntiles,
-                                                                      L.counter, L.lay);
-  e = cudaGetLastError();
+  e = launch_dependent(hc_batch_scan_kernel, static_cast<unsigned>(L.grid_scan), kThreads, L.smem_scan, stream,
+                       !t1.active() && !t0.active(), L.args, L.tiles, L.ntiles, L.counter, L.lay);
+  if (e == cudaSuccess) e = cudaGetLastError();
   timing_end(t1, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_batch_scan_kernel launch");
   TimingToken t2 = timing_begin(kKindEmit, stream);
-  hc_batch_emit_kernel<<<static_cast<unsigned>(L.netiles * kEmitSplit), kThreads, L.smem_emit, stream>>>(
-      L.args, L.etiles);
-  e = cudaGetLastError();
+  e = launch_dependent(hc_batch_emit_kernel, static_cast<unsigned>(L.netiles * kEmitSplit), kThreads, L.smem_emit,
+                       stream, !t2.active(), L.args, L.etiles);
+  if (e == cudaSuccess) e = cudaGetLastError();
   timing_end(t2, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_batch_emit_kernel launch");
   g_launches.fetch_add(3);

@@ -66,6 +66,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Programmatic dependent launch (sm_90 and later): a kernel that calls
+// pdl_launch_dependents lets the next kernel of its stream, when that one was
+// launched with programmatic stream serialization, start before it ends; the
+// dependent kernel's pdl_wait returns once this grid has completed and its
+// memory operations are visible.  Without the launch attribute both are
+// no-ops and the kernels run one after the other as usual.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Waits for phase `parity` of `bar` to complete; false if the wait gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "hc.h"
@@ -70,7 +71,28 @@ bool timing_enabled();
 struct TimingToken {
   cudaEvent_t ev0 = nullptr;
   int kind = -1;
+  bool active() const { return ev0 != nullptr; }
 };
+
+// Launches kernel fn on `stream`; with pdl, as a programmatic dependent of
+// the kernel before it in the stream (which must call pdl_launch_dependents
+// and fn must call pdl_wait before reading that kernel's results): the launch
+// and the kernel's prologue overlap the previous kernel's tail.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*fn)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                             cudaStream_t stream, bool pdl, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
+}
 TimingToken timing_begin(int kind, cudaStream_t stream);
 void timing_end(const TimingToken& t, cudaStream_t stream);
 

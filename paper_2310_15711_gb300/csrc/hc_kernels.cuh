@@ -411,16 +411,19 @@ __device__ __forceinline__ void warp_stream(const SearchArgs& a, unsigned long l
   sink.slot = slots + tid;
   bool ok = true;
   int i = 0;
-  for (; i < nchunks; ++i) {
-    const int st = i % nst;
+  // ring slot and mbarrier phase of chunk i, kept incrementally (no runtime
+  // division by the ring size in the loop)
+  int st = 0, prev_st = nst - 1;
+  uint32_t phase = 0;
+  for (; i < nchunks; ++i, prev_st = st, st = (st + 1 == nst) ? 0 : st + 1, phase ^= (st == 0) ? 1u : 0u) {
     const unsigned long long c = c0 + static_cast<unsigned long long>(i);
     if constexpr (STAGED) {
       if (lane == 0 && i > 0 && i + nst - 1 < nchunks) {
         // the buffer of chunk i-1 was released by the __syncwarp that ended it
         fence_proxy_async_smem();
-        issue((i + nst - 1) % nst, c + nst - 1);
+        issue(prev_st, c + nst - 1);
       }
-      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&wb[st], static_cast<uint32_t>(i / nst) & 1u));
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&wb[st], phase));
       if (!ok) break;
     }
     const unsigned long long cs = c * a.C;

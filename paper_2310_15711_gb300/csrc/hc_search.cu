@@ -59,6 +59,7 @@ template <int Q, bool STAGED>
 __global__ void __launch_bounds__(kThreads) hc_scan_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
+  pdl_launch_dependents();  // the emit kernel may be scheduled; it waits for this grid
 
   const int tid = threadIdx.x, warp = tid >> 5;
   uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
@@ -95,6 +96,7 @@ template <int Q>
 __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
+  pdl_launch_dependents();
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned long long w_id = static_cast<unsigned long long>(blockIdx.x) * kWarps + warp;
@@ -151,15 +153,18 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
   unsigned long long overflow = kNoOverflow;
   bool ok = true;
   int i = 0;
-  for (; i < nchunks; ++i) {
-    const int st = i % nst;
+  // ring slot and mbarrier phase of chunk i, kept incrementally (no runtime
+  // division by the ring size in the loop)
+  int st = 0, prev_st = nst - 1;
+  uint32_t phase = 0;
+  for (; i < nchunks; ++i, prev_st = st, st = (st + 1 == nst) ? 0 : st + 1, phase ^= (st == 0) ? 1u : 0u) {
     const unsigned long long c = c0 + static_cast<unsigned long long>(i);
     if (lane == 0 && i > 0 && i + nst - 1 < nchunks) {
       // the buffer of chunk i-1 was released by the __syncwarp that ended it
       fence_proxy_async_smem();
-      issue((i + nst - 1) % nst, c + nst - 1);
+      issue(prev_st, c + nst - 1);
     }
-    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&wb[st], static_cast<uint32_t>(i / nst) & 1u));
+    ok = __all_sync(0xffffffffu, mbar_wait_bounded(&wb[st], phase));
     if (!ok) break;
     const unsigned long long cs = c * a.C;
     const int wins = static_cast<int>(min(static_cast<unsigned long long>(a.C), a.nwin - cs));
@@ -241,6 +246,7 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
 template <int Q>
 __global__ void __launch_bounds__(kThreads) hc_emit_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
+  pdl_wait();  // the scan grid has completed and its records are visible
   emit_group<Q>(a, blockIdx.x / kEmitSplit, blockIdx.x % kEmitSplit, smem);
 }
 
@@ -543,8 +549,9 @@ int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_
   timing_end(t0, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
   TimingToken t1 = timing_begin(kKindEmit, stream);
-  p.emit<<<static_cast<unsigned>(p.emit_ctas), kThreads, p.smem_emit, stream>>>(a);
-  e = cudaGetLastError();
+  e = launch_dependent(p.emit, static_cast<unsigned>(p.emit_ctas), kThreads, p.smem_emit, stream,
+                       !t1.active(), a);
+  if (e == cudaSuccess) e = cudaGetLastError();
   timing_end(t1, stream);
   g_launches.fetch_add(2);
   if (e != cudaSuccess) return cuda_error(e, "hc_emit_kernel launch");
@@ -569,8 +576,9 @@ int launch_planned_filter_ptrs(const Filter* f, const SearchPlan& p, const uint3
   timing_end(t0, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
   TimingToken t1 = timing_begin(kKindEmit, stream);
-  p.emit<<<static_cast<unsigned>(p.emit_ctas), kThreads, p.smem_emit, stream>>>(a);
-  e = cudaGetLastError();
+  e = launch_dependent(p.emit, static_cast<unsigned>(p.emit_ctas), kThreads, p.smem_emit, stream,
+                       !t1.active(), a);
+  if (e == cudaSuccess) e = cudaGetLastError();
   timing_end(t1, stream);
   g_launches.fetch_add(2);
   if (e != cudaSuccess) return cuda_error(e, "hc_emit_kernel launch");
