@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--patterns", type=int, default=100, help="patterns per (sigma, m) cell")
     ap.add_argument("--n", type=int, default=1 << 28, help="text length per sigma")
+    ap.add_argument("--params", choices=["tuned", "paper"], default="tuned",
+                    help="(q, alpha) and launch options per cell: measured by the autotuner on this "
+                         "GPU (default), or the paper's Tables 1-3")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -81,7 +84,10 @@ def workload_config(args):
         "ms": list(hi.SWEEP_MS),
         "patterns_per_cell": args.patterns,
         "text": "i.i.d. uniform uint8, seeds 100+sigma; patterns copied from the text",
-        "q_alpha": "paper's choice per text type and m (Tables 1-3), q clamped to m",
+        "q_alpha": ("autotuned per (sigma, m) on this GPU (calibration texts of the same kind, not the "
+                    "sweep's); paper_params gives the sweep on Tables 1-3"
+                    if getattr(args, "params", "paper") == "tuned" else
+                    "paper's choice per text type and m (Tables 1-3), q clamped to m"),
         "l2": "inputs larger than L2 (256 MiB texts vs 129 MB L2); no flush",
     }
 
@@ -146,11 +152,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def scan_family(m: int, q: int) -> str:
-    """The scan kernel the library picks for a pattern (its automatic mode)."""
+def scan_family(m: int, q: int, mode: int = 0) -> str:
+    """The scan kernel a search runs: the given mode, else the library's
+    automatic choice."""
+    if mode:
+        return {1: "scan_staged", 2: "scan_direct", 3: "scan_dense"}[mode]
     if m == q:
         return "scan_dense"
-    if m - q + 1 >= 200:
+    if m - q + 1 >= 200 or m > 16384:
         return "scan_direct"
     return "scan_staged"
 
@@ -252,20 +261,43 @@ def run_gpu(args, rank, world, local_rank):
     hc.build()
     hc.lib()
 
+    # ---- parameters: measured per (sigma, m) on this GPU by the autotuner
+    # (single-search path, its own calibration texts), unless --params paper
+    tune_s = None
+    tuner = None
+    if args.params == "tuned":
+        tuner = hc.HCTuner()
+        t0 = time.perf_counter()
+        tuner.calibrate(hi.SWEEP_SIGMAS, hi.SWEEP_MS, text_bytes=args.n, seed=21, path=hc.HC_TUNE_SINGLE)
+        torch.cuda.synchronize(dev)
+        tune_s = time.perf_counter() - t0
+
     # ---- inputs
     texts_np = {s: hi.sweep_text(s, args.n) for s in hi.SWEEP_SIGMAS}
     texts = {s: torch.from_numpy(t).to(dev) for s, t in texts_np.items()}
-    cells = {}
-    for s in hi.SWEEP_SIGMAS:
-        for m in hi.SWEEP_MS:
-            pats = hi.sweep_patterns(texts_np[s], s, m, args.patterns)
-            q, alpha = hi.paper_q_alpha(s, m)
-            filters = []
-            for x in pats:
-                f = hc.hc_preprocess(x, q, alpha)
-                f.to_device()
-                filters.append(f)
-            cells[(s, m)] = (pats, filters, q, alpha)
+
+    def make_cells(kind):
+        out = {}
+        for s in hi.SWEEP_SIGMAS:
+            for m in hi.SWEEP_MS:
+                pats = hi.sweep_patterns(texts_np[s], s, m, args.patterns)
+                opts = None
+                if kind == "tuned":
+                    e = tuner.lookup(s, m)
+                    q, alpha = e["q"], e["alpha"]
+                    opts = hc.SearchOpts(lane_bytes=e["lane_bytes"], mode=e["mode"])
+                else:
+                    q, alpha = hi.paper_q_alpha(s, m)
+                filters = []
+                for x in pats:
+                    f = hc.hc_preprocess(x, q, alpha)
+                    f.to_device()
+                    filters.append(f)
+                out[(s, m)] = (pats, filters, q, alpha, opts)
+        return out
+
+    cells = make_cells(args.params)
+    paper_cells = make_cells("paper") if args.params == "tuned" else None
     cap = 1 << 27
     pos = torch.empty(cap, dtype=torch.int64, device=dev)
     ncell = len(cells)
@@ -273,14 +305,15 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     keys = list(cells.keys())
 
-    def one_step(cell_events=None):
+    def one_step(cell_events=None, which=None):
+        which = cells if which is None else which
         for ci, key in enumerate(keys):
-            pats, filters, q, alpha = cells[key]
+            pats, filters, q, alpha, opts = which[key]
             y = texts[key[0]]
             if cell_events is not None:
                 cell_events[ci][0].record(stream)
             for pi, f in enumerate(filters):
-                hc.hc_search_async(f, y, pos, counts[ci, pi:pi + 1], cap=cap, stream=stream)
+                hc.hc_search_ex(f, y, pos, counts[ci, pi:pi + 1], opts, cap=cap, stream=stream)
             if cell_events is not None:
                 cell_events[ci][1].record(stream)
 
@@ -330,6 +363,28 @@ def run_gpu(args, rank, world, local_rank):
     hc.hc_timing_enable(False)
     kernel_times = hc.hc_timing_report(reset=True)   # {family: (ms, launches)}
     hc.hc_check_status(stream)
+    counts_tuned = counts.clone()
+    paper = None
+    if paper_cells is not None:
+        # the same sweep on the paper's (q, alpha) (Tables 1-3), for comparison
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                one_step(which=paper_cells)
+        barrier()
+        pe0, pe1 = ev(), ev()
+        pe0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                one_step(which=paper_cells)
+        pe1.record(stream)
+        barrier()
+        hc.hc_check_status(stream)
+        p_s, p_bytes = combine_ranks(pe0.elapsed_time(pe1) / 1e3,
+                                     sum(texts[s].numel() * args.patterns for (s, m) in keys) * args.steps,
+                                     dist, dev)
+        paper = {"value": round(p_bytes / p_s / GB, 2), "unit": UNIT,
+                 "counts_equal": bool(torch.equal(counts, counts_tuned))}
+        counts.copy_(counts_tuned)
     step_ms = float(sum(e[0].elapsed_time(e[1]) for e in step_ev))
     cell_ms = np.array([sum(cell_ev[k][ci][0].elapsed_time(cell_ev[k][ci][1])
                             for k in range(args.steps)) for ci in range(ncell)])
@@ -346,15 +401,16 @@ def run_gpu(args, rank, world, local_rank):
     fam_bytes = {}
     per_cell = {}
     for ci, (s, m) in enumerate(keys):
-        pats, filters, q, alpha = cells[(s, m)]
+        pats, filters, q, alpha, opts = cells[(s, m)]
         n = texts[s].numel()
         occ = float(cnt[ci].sum())
-        fam = scan_family(m, q)
+        fam = scan_family(m, q, opts.mode if opts is not None else 0)
         fam_bytes[fam] = fam_bytes.get(fam, 0.0) + n * args.patterns + 4 * occ
         fam_bytes["emit"] = fam_bytes.get("emit", 0.0) + 12 * occ
         per_cell[f"s{s}_m{m}"] = {
             "GBps": round(n * args.patterns * args.steps / (cell_ms[ci] / 1e3) / GB, 1),
             "kernel": fam, "q": q, "alpha": alpha,
+            "lane_bytes": opts.lane_bytes if opts is not None else 0,
             "occ_per_pattern": float(cnt[ci].mean()),
         }
     dominant = max(kernel_times, key=lambda k: kernel_times[k][0])
@@ -381,6 +437,9 @@ def run_gpu(args, rank, world, local_rank):
         "cells": per_cell,
         "wall_s_timed": round(wall, 3),
     }
+    if paper is not None:
+        line["paper_params"] = paper
+        line["tune_s"] = round(tune_s, 2)
 
     # ---- end to end through the synchronous C-ABI call, host buffers
     if not args.no_e2e:
@@ -393,6 +452,11 @@ def run_gpu(args, rank, world, local_rank):
     for key in keys:
         for f in cells[key][1]:
             f.free()
+        if paper_cells is not None:
+            for f in paper_cells[key][1]:
+                f.free()
+    if tuner is not None:
+        tuner.free()
 
 
 BATCH_TUNE_MS = (4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512)
@@ -705,7 +769,7 @@ def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream, dist=None):
             for key in keys:
                 if key[0] != s:
                     continue
-                pats, filters, q, alpha = cells[key]
+                pats, filters, q, alpha, _ = cells[key]
                 for x, f in zip(pats, filters):
                     count = hc.hc_search(f, x, y_dev[:n], pos, cap, stream=stream)
                     host_pos[:count].copy_(pos[:count], non_blocking=True)

@@ -271,20 +271,25 @@ void hc_batch_destroy(hc_batch *b);
  *   text_bytes bytes drawn i.i.d. uniform over sigma symbols on the device
  *   (seeded), for every m of `ms` a pattern copied from it; each candidate
  *   (q in [1, min(8, m)], alpha in [8, 13]; then, for the best pair,
- *   lane_bytes halved and doubled and both scan modes) runs as a one-query
- *   batch, best of 3 timed runs; the fastest fills the (sigma, m) cell,
- *   replacing an older one.  Synchronous on `stream`; allocates and frees
- *   device memory (text_bytes plus workspace).
+ *   lane_bytes halved and doubled and each scan mode) is timed, best of 3
+ *   runs after one untimed: path HC_TUNE_BATCHED runs it as a one-query
+ *   batch (the kernels of hc_batch_run), HC_TUNE_SINGLE as a single search
+ *   (hc_search_ex, host-built filter; its dense mode for m = q).  The
+ *   fastest fills the (sigma, m) cell, replacing an older one.  Synchronous
+ *   on `stream`; allocates and frees device memory (text_bytes plus
+ *   workspace).  A table from HC_TUNE_SINGLE may hold HC_MODE_DENSE cells
+ *   (q = m); batches and servers run those in the automatic mode.
  * hc_tuner_lookup: the cell nearest to (sigma, m) on log scales, q clamped
  *   to m (the paper's choice when the table is empty).
  * hc_tuner_save / hc_tuner_load: the table as text, one cell per line
  *   ("sigma m q alpha lane_bytes mode gbps"); load adds to the table.
  * Errors: HC_ERR_ARG, HC_ERR_NOMEM, HC_ERR_CUDA; HC_ERR_STATE for an
  * unreadable or malformed file. */
+enum { HC_TUNE_BATCHED = 0, HC_TUNE_SINGLE = 1 };
 int hc_tuner_create(hc_tuner **out);
 int hc_tuner_calibrate(hc_tuner *t, const int *sigmas, size_t nsigma,
                        const uint64_t *ms, size_t nm, uint64_t text_bytes,
-                       uint64_t seed, hc_stream_t stream);
+                       uint64_t seed, int path, hc_stream_t stream);
 int hc_tuner_lookup(const hc_tuner *t, double sigma, uint64_t m,
                     hc_tune_entry *out);
 /* Number of cells, and cell i of the table (sorted by sigma, then m). */

@@ -76,7 +76,7 @@ SIGNATURES = {
     "hc_tuner_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
     "hc_tuner_calibrate": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), _sz,
                                           ctypes.POINTER(ctypes.c_uint64), _sz, ctypes.c_uint64,
-                                          ctypes.c_uint64, _vp]),
+                                          ctypes.c_uint64, ctypes.c_int, _vp]),
     "hc_tuner_lookup": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _vp]),
     "hc_tuner_size": (ctypes.c_int, [_vp, ctypes.POINTER(_sz)]),
     "hc_tuner_entry": (ctypes.c_int, [_vp, _sz, _vp]),
@@ -161,6 +161,9 @@ HC_MODE_AUTO = 0
 HC_MODE_STAGED = 1
 HC_MODE_DIRECT = 2
 HC_MODE_DENSE = 3
+
+HC_TUNE_BATCHED = 0
+HC_TUNE_SINGLE = 1
 
 
 class SearchOpts(ctypes.Structure):
@@ -339,11 +342,13 @@ class HCTuner:
             raise ValueError("tuner has been freed")
         return self._h
 
-    def calibrate(self, sigmas, ms, text_bytes=256 << 20, seed=1, stream=None):
+    def calibrate(self, sigmas, ms, text_bytes=256 << 20, seed=1, path=0, stream=None):
+        """path: HC_TUNE_BATCHED (0, the batched kernels) or HC_TUNE_SINGLE (1)."""
         sa = (ctypes.c_int * len(sigmas))(*[int(v) for v in sigmas])
         ma = (ctypes.c_uint64 * len(ms))(*[int(v) for v in ms])
         _check(lib().hc_tuner_calibrate(self.handle, sa, len(sigmas), ma, len(ms), int(text_bytes),
-                                        int(seed), _stream_handle(stream)), "hc_tuner_calibrate")
+                                        int(seed), int(path), _stream_handle(stream)),
+               "hc_tuner_calibrate")
 
     def lookup(self, sigma: float, m: int) -> dict:
         e = TuneEntry()

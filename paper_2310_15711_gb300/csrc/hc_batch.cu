@@ -292,7 +292,7 @@ int plan_add_query(BatchPlan& plan, const hc_batch_query& Q, size_t i, const Que
   a.C = 32u * static_cast<uint32_t>(L);
   a.stages = direct ? 0 : 2;
   a.head = static_cast<int>(reinterpret_cast<uintptr_t>(Q.y_dev) & 15u);
-  a.stage_bytes = direct ? 0u : static_cast<uint32_t>(((16 + a.C + Q.m - 1 + 15) & ~uint64_t(15)) + 64);
+  a.stage_bytes = direct ? 0u : stage_bytes_for(a.C, Q.m, false);
   a.x_smem = Q.m <= 4096 ? static_cast<uint32_t>((Q.m + 15) & ~uint64_t(15)) : 0u;
   plan.lay.x_bytes = std::max(plan.lay.x_bytes, a.x_smem);
   plan.lay.ring_bytes = std::max(plan.lay.ring_bytes, static_cast<uint32_t>(a.stages) * a.stage_bytes);
@@ -516,6 +516,7 @@ int create_batch(const hc_batch_query* qs, size_t nq, const hc_tuner* tuner, hc_
       double sigma = Q.sigma;
       if (Q.sigma <= 0) sigma = est[k++];
       p = tuner_lookup(t, sigma, Q.m);
+      if (p.mode == HC_MODE_DENSE) p.mode = HC_MODE_AUTO;  // a single-search table: m = q runs staged here
       if (Q.lane_bytes > 0) p.lane_bytes = Q.lane_bytes;
       if (Q.mode != HC_MODE_AUTO) p.mode = Q.mode;
     } else {

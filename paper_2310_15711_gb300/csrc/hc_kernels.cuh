@@ -15,7 +15,7 @@ namespace hc {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxStages = 4;
-constexpr int kSlots = 4;
+constexpr int kSlots = 2;
 constexpr int kMaxSmemX = 4096;             // larger patterns verify from global memory
 constexpr size_t kMaxStagedM = 16384;       // larger patterns use the unstaged kernel
 constexpr unsigned long long kNoOverflow = ~0ull;
@@ -23,6 +23,14 @@ constexpr int kDirectShift = 200;
 constexpr int kEmitSplit = 2;               // CTAs of the emit kernel per record group
 constexpr int kMaxEmitGroup = 64;           // records per emit record group, at most           // shifts this long skip most 32-byte sectors
 
+
+// Bytes of one staging buffer: head (< 16) + C + m - 1 bytes of text rounded
+// up to 16, plus 16 bytes of slack for the per-lane kernels (their word loads
+// end at most 11 bytes past the last q-gram's first byte) or 32 for the dense
+// kernel (its 16-byte loads end at most 20 bytes past the last window start).
+inline uint32_t stage_bytes_for(uint32_t C, uint64_t m, bool dense) {
+  return static_cast<uint32_t>(((16 + C + m - 1 + 15) & ~uint64_t(15)) + (dense ? 32 : 16));
+}
 
 struct SearchArgs {
   unsigned int* status;      // device status word: bit 0 set when a bounded wait gave up

@@ -397,9 +397,10 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   const size_t fbytes = (f->F.size() * 4 + 15) & ~size_t(15);
   const size_t slot_bytes = size_t(kSlots) * kThreads * 4;
   // staged text: head (< 16) + C + m - 1 bytes, rounded to 16, plus slack for
-  // the word loads that run past the last q-gram (at most 20 bytes past the
-  // chunk's last window start in the dense kernel, 12 in the others)
-  p.stage_bytes = static_cast<uint32_t>(((16 + p.C + f->m - 1 + 15) & ~size_t(15)) + 64);
+  // the loads that run past the copied bytes: the per-lane kernels read at
+  // most 11 bytes past the last q-gram's first byte (three 32-bit words), the
+  // dense kernel at most 20 past the chunk's last window start
+  p.stage_bytes = stage_bytes_for(p.C, f->m, kind == HC_MODE_DENSE);
   if (kind == HC_MODE_DENSE) {
     // one ring of `stages` buffers per warp
     p.scan = dense_kernel_for_q(f->q);
@@ -407,7 +408,7 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
     if (mode == HC_MODE_AUTO && p.smem_scan + static_smem(p.scan) > di.smem_optin) {
       kind = HC_MODE_STAGED;  // caller's lane_bytes too large for per-warp rings
       p.C = 32u * static_cast<uint32_t>(L);
-      p.stage_bytes = static_cast<uint32_t>(((16 + p.C + f->m - 1 + 15) & ~size_t(15)) + 64);
+      p.stage_bytes = stage_bytes_for(p.C, f->m, false);
     }
   }
   p.kind = kind;

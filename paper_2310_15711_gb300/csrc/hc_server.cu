@@ -703,6 +703,7 @@ int make_request(Server* s, const hc_server_request& q, uint64_t submit_ns, Req*
   r->cap = std::min<uint64_t>(q.cap ? q.cap : s->cfg.default_cap, nwin);
   if (q.q == 0) {
     r->p = tuner_lookup(s->tuner, t.sigma, q.m);
+    if (r->p.mode == HC_MODE_DENSE) r->p.mode = HC_MODE_AUTO;  // batched kernels have no dense form
   } else {
     r->p.q = q.q;
     r->p.alpha = q.alpha;

@@ -69,7 +69,7 @@ QueryParams paper_params(double sigma, uint64_t m) {
 // plan_finish), against the opt-in limit of sm_100-class devices.
 bool staged_fits(int L, uint64_t m, int alpha) {
   const uint64_t C = 32ull * static_cast<uint64_t>(std::max(L, 1));
-  const uint64_t stage = ((16 + C + m - 1 + 15) & ~uint64_t(15)) + 64;
+  const uint64_t stage = stage_bytes_for(static_cast<uint32_t>(C), m, false);
   const uint64_t x = m <= 4096 ? ((m + 15) & ~uint64_t(15)) : 0;
   const uint64_t smem = (4ull << alpha) + x + uint64_t(kSlots) * kThreads * 4 + uint64_t(kWarps) * 2 * stage;
   return m <= static_cast<uint64_t>(kMaxStagedM) && smem + 2048 <= 232448;
@@ -216,11 +216,68 @@ int time_candidate(Scratch& sc, int dev, const uint8_t* x, uint64_t m, const uin
   return HC_OK;
 }
 
+// The same for the single-search path: a host-built filter (hc_preprocess)
+// and the two kernels of hc_search_ex (dense, staged or direct scan, emit).
+int time_candidate_single(Scratch& sc, int dev, const std::vector<uint8_t>& xh, const uint8_t* y, uint64_t n,
+                          const QueryParams& p, int reps, cudaStream_t stream, cudaEvent_t e0, cudaEvent_t e1,
+                          double* seconds, int* lane_bytes, int* mode) {
+  *seconds = INFINITY;
+  hc_filter* fh = nullptr;
+  if (hc_preprocess(xh.data(), xh.size(), p.q, p.alpha, &fh) != HC_OK) {
+    clear_error();
+    return HC_OK;
+  }
+  Filter* f = as_filter(fh);
+  hc_search_opts o{};
+  o.struct_size = sizeof o;
+  o.lane_bytes = p.lane_bytes;
+  o.mode = p.mode;
+  SearchPlan sp;
+  if (plan_search(f, n, 0, &o, dev, &sp) != HC_OK) {
+    clear_error();
+    hc_filter_free(fh);
+    return HC_OK;
+  }
+  int rc = filter_to_device(f);
+  if (rc == HC_OK) rc = grow(&sc.ws, &sc.ws_cap, sp.ws_bytes, "cudaMalloc(tuner workspace)");
+  uint64_t* count = reinterpret_cast<uint64_t*>(sc.counter + 1);
+  if (rc == HC_OK) rc = launch_planned(f, sp, y, n, nullptr, 0, count, sc.ws, stream);
+  double best = INFINITY;
+  for (int r = 0; r < reps && rc == HC_OK; ++r) {
+    cudaEventRecord(e0, stream);
+    rc = launch_planned(f, sp, y, n, nullptr, 0, count, sc.ws, stream);
+    cudaEventRecord(e1, stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      rc = cuda_error(e, "cudaEventSynchronize(tuner)");
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms * 1e-3);
+  }
+  hc_filter_free(fh);
+  if (rc != HC_OK) return rc;
+  *seconds = best;
+  *lane_bytes = sp.L;
+  *mode = sp.kind;
+  return HC_OK;
+}
+
 int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n, int sigma, uint64_t m,
-                   uint64_t seed, cudaStream_t stream, cudaEvent_t e0, cudaEvent_t e1) {
+                   uint64_t seed, int path, cudaStream_t stream, cudaEvent_t e0, cudaEvent_t e1) {
   // the pattern: m bytes of the text at a seeded offset
   const uint64_t off = (seed * 0x9E3779B97F4A7C15ull ^ m * 0xBF58476D1CE4E5B9ull) % (n - m + 1);
   const uint8_t* x = y + off;
+  std::vector<uint8_t> xh(m);
+  if (path == HC_TUNE_SINGLE) {
+    cudaError_t e = cudaMemcpy(xh.data(), x, m, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(calibration pattern)");
+  }
+  auto time_it = [&](const QueryParams& p, double* s, int* L, int* mode) {
+    return path == HC_TUNE_SINGLE ? time_candidate_single(sc, dev, xh, y, n, p, 3, stream, e0, e1, s, L, mode)
+                                  : time_candidate(sc, dev, x, m, y, n, p, 3, stream, e0, e1, s, L, mode);
+  };
   double best = INFINITY;
   QueryParams bp;
   int best_L = 0, best_mode = 0;
@@ -231,7 +288,7 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
       p.alpha = alpha;
       double s = INFINITY;
       int L = 0, mode = 0;
-      int rc = time_candidate(sc, dev, x, m, y, n, p, 3, stream, e0, e1, &s, &L, &mode);
+      int rc = time_it(p, &s, &L, &mode);
       if (rc != HC_OK) return rc;
       if (s < best) {
         best = s;
@@ -242,15 +299,16 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
     }
   if (!std::isfinite(best)) return set_error(HC_ERR_ARG, "hc_tuner_calibrate: no candidate fits");
   const int L0 = best_L;
-  for (int mode : {HC_MODE_STAGED, HC_MODE_DIRECT})
+  for (int mode : {HC_MODE_STAGED, HC_MODE_DIRECT, HC_MODE_DENSE})
     for (int L : {L0 / 2, L0, L0 * 2}) {
       if (L < 1 || L > 4096 || (mode == best_mode && L == L0)) continue;
+      if (mode == HC_MODE_DENSE && (path != HC_TUNE_SINGLE || static_cast<uint64_t>(bp.q) != m)) continue;
       QueryParams p = bp;
       p.lane_bytes = L;
       p.mode = mode;
       double s = INFINITY;
       int Lr = 0, mr = 0;
-      int rc = time_candidate(sc, dev, x, m, y, n, p, 3, stream, e0, e1, &s, &Lr, &mr);
+      int rc = time_it(p, &s, &Lr, &mr);
       if (rc != HC_OK) return rc;
       if (s < best) {
         best = s;
@@ -309,8 +367,10 @@ QueryParams tuner_lookup(const Tuner* t, double sigma, uint64_t m) {
   p.mode = best.mode;
   if (best.m != m) {
     // launch options measured for another length: keep them only where they
-    // still fit (the staged form's buffers grow with m)
-    if (p.mode == HC_MODE_STAGED && !staged_fits(p.lane_bytes, m, p.alpha)) {
+    // still fit (the staged form's buffers grow with m; the dense form needs
+    // m = q)
+    if ((p.mode == HC_MODE_STAGED && !staged_fits(p.lane_bytes, m, p.alpha)) ||
+        (p.mode == HC_MODE_DENSE && static_cast<uint64_t>(p.q) != m)) {
       p.mode = HC_MODE_AUTO;
       p.lane_bytes = 0;
     }
@@ -341,7 +401,7 @@ void hc_tuner_free(hc_tuner* tp) {
 }
 
 int hc_tuner_calibrate(hc_tuner* tp, const int* sigmas, size_t nsigma, const uint64_t* ms, size_t nm,
-                       uint64_t text_bytes, uint64_t seed, hc_stream_t stream_) {
+                       uint64_t text_bytes, uint64_t seed, int path, hc_stream_t stream_) {
   clear_error();
   Tuner* t = as_tuner(tp);
   if (t == nullptr) return set_error(HC_ERR_ARG, "hc_tuner_calibrate: invalid tuner");
@@ -354,6 +414,8 @@ int hc_tuner_calibrate(hc_tuner* tp, const int* sigmas, size_t nsigma, const uin
       return set_error(HC_ERR_ARG, "hc_tuner_calibrate: m out of [1, min(65536, text_bytes)]");
   if (text_bytes < 1 || text_bytes > (uint64_t(1) << 34))
     return set_error(HC_ERR_ARG, "hc_tuner_calibrate: text_bytes out of [1, 2^34]");
+  if (path != HC_TUNE_BATCHED && path != HC_TUNE_SINGLE)
+    return set_error(HC_ERR_ARG, "hc_tuner_calibrate: path must be HC_TUNE_BATCHED or HC_TUNE_SINGLE");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -380,7 +442,7 @@ int hc_tuner_calibrate(hc_tuner* tp, const int* sigmas, size_t nsigma, const uin
     }
     g_launches.fetch_add(1);
     for (size_t mi = 0; mi < nm && rc == HC_OK; ++mi)
-      rc = calibrate_cell(t, sc, dev, y, text_bytes, sigmas[si], ms[mi], seed, stream, e0, e1);
+      rc = calibrate_cell(t, sc, dev, y, text_bytes, sigmas[si], ms[mi], seed, path, stream, e0, e1);
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -458,7 +520,8 @@ int hc_tuner_load(hc_tuner* tp, const char* path) {
                     &c.gbps) != 7 ||
         c.sigma < 1 || m < 1 || c.q < 1 || c.q > kMaxQ || static_cast<unsigned long long>(c.q) > m ||
         c.alpha < 1 || c.alpha > kMaxAlpha || c.lane_bytes < 0 || c.lane_bytes > 4096 ||
-        (c.mode != HC_MODE_AUTO && c.mode != HC_MODE_STAGED && c.mode != HC_MODE_DIRECT)) {
+        (c.mode != HC_MODE_AUTO && c.mode != HC_MODE_STAGED && c.mode != HC_MODE_DIRECT &&
+         !(c.mode == HC_MODE_DENSE && static_cast<unsigned long long>(c.q) == m))) {
       rc = set_error(HC_ERR_STATE, std::string("hc_tuner_load: malformed line ") + std::to_string(lineno));
       break;
     }

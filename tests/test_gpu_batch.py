@@ -244,3 +244,34 @@ def test_tuner_calibration_and_tuned_batch(hc):
         assert (b.params(i)["q"], b.params(i)["alpha"]) == hi.paper_q_alpha(sigma, x.size), i
     b.destroy()
     t.free()
+
+
+def test_tuner_single_search_path(hc):
+    """Calibration on the single-search kernels (dense form included for
+    m = q); searches run with the tuned (q, alpha, lane_bytes, mode) equal
+    the oracle."""
+    t = hc.HCTuner()
+    t.calibrate([2, 20], [2, 8, 40], text_bytes=4 << 20, seed=5, path=hc.HC_TUNE_SINGLE)
+    ent = t.entries()
+    assert [(e["sigma"], e["m"]) for e in ent] == [(2, 2), (2, 8), (2, 40), (20, 2), (20, 8), (20, 40)]
+    for e in ent:
+        assert 1 <= e["q"] <= min(8, e["m"]) and e["gbps"] > 0, e
+        assert e["mode"] in (1, 2, 3) and (e["mode"] != 3 or e["q"] == e["m"]), e
+    rng = np.random.default_rng(21)
+    for sigma in (2, 20):
+        y = hi.uniform_text(700_001, sigma, seed=60 + sigma)
+        y_dev = torch.from_numpy(y).cuda()
+        for m in (2, 8, 40, 17):
+            x, _ = hi.extract_pattern(y, m, rng)
+            e = t.lookup(sigma, m)
+            want = oracle.hc_search(x, y, e["q"], e["alpha"])
+            f = hc.hc_preprocess(x, e["q"], e["alpha"])
+            pos = torch.full((want.size + 1,), -1, dtype=torch.int64, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(lane_bytes=e["lane_bytes"], mode=e["mode"]))
+            torch.cuda.synchronize()
+            hc.hc_check_status()
+            assert int(cnt.item()) == want.size, (sigma, m, e)
+            assert np.array_equal(pos[:want.size].cpu().numpy().view(np.uint64), want), (sigma, m, e)
+            f.free()
+    t.free()

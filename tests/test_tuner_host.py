@@ -104,7 +104,7 @@ def test_save_load_round_trip_and_replace(hc, tmp_path):
     t2.free()
 
 
-@pytest.mark.parametrize("bad", ["4 8 9 12 0 0 1", "4 8 4 16 0 0 1", "4 8 4 12 0 7 1",
+@pytest.mark.parametrize("bad", ["4 8 9 12 0 0 1", "4 8 4 16 0 0 1", "4 8 4 12 0 7 1", "4 8 4 12 0 3 1",
                                  "4 2 3 12 0 0 1", "0 8 4 12 0 0 1", "4 8 4 12 0 0",
                                  "4 8 4 12 5000 0 1", "garbage"])
 def test_malformed_lines_rejected(hc, tmp_path, bad):
@@ -132,8 +132,26 @@ def test_invalid_arguments(hc):
     # calibration arguments are checked before any device work
     sig = (ctypes.c_int * 1)(0)
     ms = (ctypes.c_uint64 * 1)(8)
-    assert L.hc_tuner_calibrate(t.handle, sig, 1, ms, 1, 1 << 20, 1, None) == hc.HC_ERR_ARG
+    assert L.hc_tuner_calibrate(t.handle, sig, 1, ms, 1, 1 << 20, 1, 0, None) == hc.HC_ERR_ARG
     sig[0] = 4
     ms[0] = 0
-    assert L.hc_tuner_calibrate(t.handle, sig, 1, ms, 1, 1 << 20, 1, None) == hc.HC_ERR_ARG
+    assert L.hc_tuner_calibrate(t.handle, sig, 1, ms, 1, 1 << 20, 1, 0, None) == hc.HC_ERR_ARG
+    ms[0] = 8
+    assert L.hc_tuner_calibrate(t.handle, sig, 1, ms, 1, 1 << 20, 1, 7, None) == hc.HC_ERR_ARG
+    t.free()
+
+
+def test_dense_cells_only_where_m_equals_q(hc, tmp_path):
+    """A single-search table may hold dense cells (m = q); a lookup for
+    another length falls back to automatic launch options."""
+    p = str(tmp_path / "d.txt")
+    _write(p, ["2 8 8 12 16 3 900"])
+    t = hc.HCTuner()
+    t.load(p)
+    e = t.lookup(2, 8)
+    assert (e["q"], e["alpha"], e["lane_bytes"], e["mode"]) == (8, 12, 16, 3)
+    e = t.lookup(2, 10)            # q = 8 != m = 10: no dense form
+    assert (e["q"], e["mode"], e["lane_bytes"]) == (8, 0, 0)
+    e = t.lookup(2, 6)             # q clamped to 6 = m: dense is valid again but the cell's L was for m = 8
+    assert e["q"] == 6
     t.free()
