@@ -122,6 +122,10 @@ struct Scratch {
   size_t filters_cap = 0;
   uint8_t* ws = nullptr;
   size_t ws_cap = 0;
+  uint8_t* fx = nullptr;        // single path: filter words + pattern (device)
+  size_t fx_cap = 0;
+  uint8_t* host = nullptr;      // pinned staging of launch tables / filters
+  size_t host_cap = 0;
   ~Scratch() {
     cudaFree(args);
     cudaFree(tiles);
@@ -129,8 +133,24 @@ struct Scratch {
     cudaFree(counter);
     cudaFree(filters);
     cudaFree(ws);
+    cudaFree(fx);
+    cudaFreeHost(host);
   }
 };
+
+int grow_host(Scratch& sc, size_t need) {
+  if (need <= sc.host_cap && sc.host != nullptr) return HC_OK;
+  cudaFreeHost(sc.host);
+  sc.host = nullptr;
+  sc.host_cap = 0;
+  const size_t n = std::max<size_t>(need * 2, 1 << 16);
+  void* v = nullptr;
+  cudaError_t e = cudaHostAlloc(&v, n, cudaHostAllocDefault);
+  if (e != cudaSuccess) return cuda_error(e, "cudaHostAlloc(tuner staging)");
+  sc.host = static_cast<uint8_t*>(v);
+  sc.host_cap = n;
+  return HC_OK;
+}
 
 template <typename T>
 int grow(T** p, size_t* cap, size_t need, const char* what) {
@@ -175,13 +195,19 @@ int time_candidate(Scratch& sc, int dev, const uint8_t* x, uint64_t m, const uin
   if (rc == HC_OK) rc = grow(&sc.ws, &sc.ws_cap, plan.ws_bytes, "cudaMalloc(tuner workspace)");
   if (rc != HC_OK) return rc;
   plan_bind(plan, sc.filters, sc.ws);
-  cudaError_t e = cudaMemcpyAsync(sc.args, plan.args.data(), sizeof(SearchArgs), cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess && !plan.tiles.empty())
-    e = cudaMemcpyAsync(sc.tiles, plan.tiles.data(), plan.tiles.size() * sizeof(BatchTile),
-                        cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess && !plan.etiles.empty())
-    e = cudaMemcpyAsync(sc.etiles, plan.etiles.data(), plan.etiles.size() * sizeof(EmitTile),
-                        cudaMemcpyHostToDevice, stream);
+  // the tables go through pinned staging (pageable copies would synchronise);
+  // the previous candidate's copies have completed (its runs were waited for)
+  const size_t tb = plan.tiles.size() * sizeof(BatchTile), eb = plan.etiles.size() * sizeof(EmitTile);
+  rc = grow_host(sc, sizeof(SearchArgs) + tb + eb);
+  if (rc != HC_OK) return rc;
+  std::memcpy(sc.host, plan.args.data(), sizeof(SearchArgs));
+  std::memcpy(sc.host + sizeof(SearchArgs), plan.tiles.data(), tb);
+  std::memcpy(sc.host + sizeof(SearchArgs) + tb, plan.etiles.data(), eb);
+  cudaError_t e = cudaMemcpyAsync(sc.args, sc.host, sizeof(SearchArgs), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess && tb)
+    e = cudaMemcpyAsync(sc.tiles, sc.host + sizeof(SearchArgs), tb, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess && eb)
+    e = cudaMemcpyAsync(sc.etiles, sc.host + sizeof(SearchArgs) + tb, eb, cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(tuner tables)");
   BatchLaunch L;
   L.args = sc.args;
@@ -238,14 +264,26 @@ int time_candidate_single(Scratch& sc, int dev, const std::vector<uint8_t>& xh, 
     hc_filter_free(fh);
     return HC_OK;
   }
-  int rc = filter_to_device(f);
-  if (rc == HC_OK) rc = grow(&sc.ws, &sc.ws_cap, sp.ws_bytes, "cudaMalloc(tuner workspace)");
+  // the filter words and the pattern through pinned staging into a reused
+  // device buffer (no per-candidate allocation)
+  const size_t fbytes = (f->F.size() * 4 + 15) & ~size_t(15);
+  int rc = grow(&sc.ws, &sc.ws_cap, sp.ws_bytes, "cudaMalloc(tuner workspace)");
+  if (rc == HC_OK) rc = grow(&sc.fx, &sc.fx_cap, fbytes + f->x.size(), "cudaMalloc(tuner filter)");
+  if (rc == HC_OK) rc = grow_host(sc, fbytes + f->x.size());
+  if (rc == HC_OK) {
+    std::memcpy(sc.host, f->F.data(), f->F.size() * 4);
+    std::memcpy(sc.host + fbytes, f->x.data(), f->x.size());
+    cudaError_t e = cudaMemcpyAsync(sc.fx, sc.host, fbytes + f->x.size(), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpyAsync(tuner filter)");
+  }
+  const uint32_t* F_dev = reinterpret_cast<const uint32_t*>(sc.fx);
+  const uint8_t* x_dev = sc.fx + fbytes;
   uint64_t* count = reinterpret_cast<uint64_t*>(sc.counter + 1);
-  if (rc == HC_OK) rc = launch_planned(f, sp, y, n, nullptr, 0, count, sc.ws, stream);
+  if (rc == HC_OK) rc = launch_planned_filter_ptrs(f, sp, F_dev, x_dev, y, n, nullptr, 0, count, sc.ws, stream);
   double best = INFINITY;
   for (int r = 0; r < reps && rc == HC_OK; ++r) {
     cudaEventRecord(e0, stream);
-    rc = launch_planned(f, sp, y, n, nullptr, 0, count, sc.ws, stream);
+    rc = launch_planned_filter_ptrs(f, sp, F_dev, x_dev, y, n, nullptr, 0, count, sc.ws, stream);
     cudaEventRecord(e1, stream);
     cudaError_t e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) {
