@@ -270,11 +270,13 @@ void hc_batch_destroy(hc_batch *b);
  * hc_tuner_calibrate: for every sigma of `sigmas` a calibration text of
  *   text_bytes bytes drawn i.i.d. uniform over sigma symbols on the device
  *   (seeded), for every m of `ms` a pattern copied from it; each candidate
- *   (q in [1, min(8, m)], alpha in [8, 13]; then, for the best pair,
- *   lane_bytes halved and doubled and each scan mode) is timed, best of 3
- *   runs after one untimed: path HC_TUNE_BATCHED runs it as a one-query
- *   batch (the kernels of hc_batch_run), HC_TUNE_SINGLE as a single search
- *   (hc_search_ex, host-built filter; its dense mode for m = q).  The
+ *   (q in [1, min(8, m)], alpha in [8, 13]) is screened by one run on the
+ *   first 8 MiB of the text; the 4 fastest, then for the best of them
+ *   lane_bytes halved and doubled and each scan mode, are timed on the
+ *   whole text, best of 3 runs after one untimed.  Path HC_TUNE_BATCHED
+ *   runs a candidate as a one-query batch (the kernels of hc_batch_run),
+ *   HC_TUNE_SINGLE as a single search (hc_search_ex, host-built filter; its
+ *   dense mode for m = q).  The
  *   fastest fills the (sigma, m) cell, replacing an older one.  Synchronous
  *   on `stream`; allocates and frees device memory (text_bytes plus
  *   workspace).  A table from HC_TUNE_SINGLE may hold HC_MODE_DENSE cells

@@ -23,6 +23,8 @@
 namespace hc {
 
 constexpr uint32_t kTunerMagic = 0x48435455u;  // "HCTU"
+constexpr uint64_t kScreenBytes = 8ull << 20;  // text per screening run
+constexpr size_t kFinalists = 4;                // candidates timed on the whole text
 
 struct Tuner {
   uint32_t magic = kTunerMagic;
@@ -170,8 +172,8 @@ int grow(T** p, size_t* cap, size_t need, const char* what) {
 // Best of `reps` timed runs (after one untimed) of the one-query batch of
 // (x, y) with parameters p; +inf when the parameters do not fit.
 int time_candidate(Scratch& sc, int dev, const uint8_t* x, uint64_t m, const uint8_t* y, uint64_t n,
-                   const QueryParams& p, int reps, cudaStream_t stream, cudaEvent_t e0, cudaEvent_t e1,
-                   double* seconds, int* lane_bytes, int* mode) {
+                   const QueryParams& p, int reps, bool warm, cudaStream_t stream, cudaEvent_t e0,
+                   cudaEvent_t e1, double* seconds, int* lane_bytes, int* mode) {
   *seconds = INFINITY;
   hc_batch_query Q{};
   Q.x_dev = x;
@@ -223,7 +225,7 @@ int time_candidate(Scratch& sc, int dev, const uint8_t* x, uint64_t m, const uin
   L.smem_emit = plan.smem_emit;
   rc = batch_grid(plan, dev, &L.grid_scan);
   if (rc != HC_OK) return rc;
-  rc = launch_batch(L, stream);
+  if (warm) rc = launch_batch(L, stream);
   double best = INFINITY;
   for (int r = 0; r < reps && rc == HC_OK; ++r) {
     cudaEventRecord(e0, stream);
@@ -245,8 +247,8 @@ int time_candidate(Scratch& sc, int dev, const uint8_t* x, uint64_t m, const uin
 // The same for the single-search path: a host-built filter (hc_preprocess)
 // and the two kernels of hc_search_ex (dense, staged or direct scan, emit).
 int time_candidate_single(Scratch& sc, int dev, const std::vector<uint8_t>& xh, const uint8_t* y, uint64_t n,
-                          const QueryParams& p, int reps, cudaStream_t stream, cudaEvent_t e0, cudaEvent_t e1,
-                          double* seconds, int* lane_bytes, int* mode) {
+                          const QueryParams& p, int reps, bool warm, cudaStream_t stream, cudaEvent_t e0,
+                          cudaEvent_t e1, double* seconds, int* lane_bytes, int* mode) {
   *seconds = INFINITY;
   hc_filter* fh = nullptr;
   if (hc_preprocess(xh.data(), xh.size(), p.q, p.alpha, &fh) != HC_OK) {
@@ -279,7 +281,7 @@ int time_candidate_single(Scratch& sc, int dev, const std::vector<uint8_t>& xh, 
   const uint32_t* F_dev = reinterpret_cast<const uint32_t*>(sc.fx);
   const uint8_t* x_dev = sc.fx + fbytes;
   uint64_t* count = reinterpret_cast<uint64_t*>(sc.counter + 1);
-  if (rc == HC_OK) rc = launch_planned_filter_ptrs(f, sp, F_dev, x_dev, y, n, nullptr, 0, count, sc.ws, stream);
+  if (rc == HC_OK && warm) rc = launch_planned_filter_ptrs(f, sp, F_dev, x_dev, y, n, nullptr, 0, count, sc.ws, stream);
   double best = INFINITY;
   for (int r = 0; r < reps && rc == HC_OK; ++r) {
     cudaEventRecord(e0, stream);
@@ -312,13 +314,22 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
     cudaError_t e = cudaMemcpy(xh.data(), x, m, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(calibration pattern)");
   }
-  auto time_it = [&](const QueryParams& p, double* s, int* L, int* mode) {
-    return path == HC_TUNE_SINGLE ? time_candidate_single(sc, dev, xh, y, n, p, 3, stream, e0, e1, s, L, mode)
-                                  : time_candidate(sc, dev, x, m, y, n, p, 3, stream, e0, e1, s, L, mode);
+  // timed on the first nn bytes of the text: reps runs (after an untimed one when warm)
+  auto time_it = [&](const QueryParams& p, uint64_t nn, int reps, bool warm, double* s, int* L, int* mode) {
+    return path == HC_TUNE_SINGLE
+               ? time_candidate_single(sc, dev, xh, y, nn, p, reps, warm, stream, e0, e1, s, L, mode)
+               : time_candidate(sc, dev, x, m, y, nn, p, reps, warm, stream, e0, e1, s, L, mode);
   };
-  double best = INFINITY;
-  QueryParams bp;
-  int best_L = 0, best_mode = 0;
+  // screening: every (q, alpha) once on a prefix of the text (a poor
+  // candidate can be orders of magnitude slower than a good one: every
+  // window passing the first test and walking far); the best few are then
+  // timed on the whole text
+  struct Cand {
+    double s;
+    QueryParams p;
+  };
+  std::vector<Cand> screened;
+  const uint64_t n_screen = std::min<uint64_t>(n, std::max<uint64_t>(kScreenBytes, 64 * m));
   for (int q = 1; q <= static_cast<int>(std::min<uint64_t>(8, m)); ++q)
     for (int alpha = 8; alpha <= 13; ++alpha) {
       QueryParams p;
@@ -326,15 +337,27 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
       p.alpha = alpha;
       double s = INFINITY;
       int L = 0, mode = 0;
-      int rc = time_it(p, &s, &L, &mode);
+      int rc = time_it(p, n_screen, 1, false, &s, &L, &mode);
       if (rc != HC_OK) return rc;
-      if (s < best) {
-        best = s;
-        bp = p;
-        best_L = L;
-        best_mode = mode;
-      }
+      if (std::isfinite(s)) screened.push_back({s, p});
     }
+  if (screened.empty()) return set_error(HC_ERR_ARG, "hc_tuner_calibrate: no candidate fits");
+  std::sort(screened.begin(), screened.end(), [](const Cand& a, const Cand& b) { return a.s < b.s; });
+  double best = INFINITY;
+  QueryParams bp;
+  int best_L = 0, best_mode = 0;
+  for (size_t k = 0; k < screened.size() && k < kFinalists; ++k) {
+    double s = INFINITY;
+    int L = 0, mode = 0;
+    int rc = time_it(screened[k].p, n, 3, true, &s, &L, &mode);
+    if (rc != HC_OK) return rc;
+    if (s < best) {
+      best = s;
+      bp = screened[k].p;
+      best_L = L;
+      best_mode = mode;
+    }
+  }
   if (!std::isfinite(best)) return set_error(HC_ERR_ARG, "hc_tuner_calibrate: no candidate fits");
   const int L0 = best_L;
   for (int mode : {HC_MODE_STAGED, HC_MODE_DIRECT, HC_MODE_DENSE})
@@ -346,7 +369,7 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
       p.mode = mode;
       double s = INFINITY;
       int Lr = 0, mr = 0;
-      int rc = time_it(p, &s, &Lr, &mr);
+      int rc = time_it(p, n, 3, true, &s, &Lr, &mr);
       if (rc != HC_OK) return rc;
       if (s < best) {
         best = s;
