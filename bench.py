@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--patterns", type=int, default=100, help="patterns per (sigma, m) cell")
     ap.add_argument("--n", type=int, default=1 << 28, help="text length per sigma")
+    ap.add_argument("--cells", default="",
+                    help="comma-separated sigma:m cells to run instead of the whole sweep "
+                         "(a small case for profiling, e.g. 4:4); the line is then not the headline")
     ap.add_argument("--params", choices=["tuned", "paper"], default="tuned",
                     help="(q, alpha) and launch options per cell: measured by the autotuner on this "
                          "GPU (default), or the paper's Tables 1-3")
@@ -81,6 +84,7 @@ def workload_config(args):
         "workload": "plain HC sweep",
         "text_bytes_per_sigma": args.n,
         "sigmas": list(hi.SWEEP_SIGMAS),
+        "cells": args.cells or "all",
         "ms": list(hi.SWEEP_MS),
         "patterns_per_cell": args.patterns,
         "text": "i.i.d. uniform uint8, seeds 100+sigma; patterns copied from the text",
@@ -263,37 +267,41 @@ def run_gpu(args, rank, world, local_rank):
 
     # ---- parameters: measured per (sigma, m) on this GPU by the autotuner
     # (single-search path, its own calibration texts), unless --params paper
+    grid = [(s, m) for s in hi.SWEEP_SIGMAS for m in hi.SWEEP_MS]
+    if args.cells:
+        grid = [tuple(int(v) for v in c.split(":")) for c in args.cells.split(",")]
+    sigmas = sorted({s for s, _ in grid})
     tune_s = None
     tuner = None
     if args.params == "tuned":
         tuner = hc.HCTuner()
         t0 = time.perf_counter()
-        tuner.calibrate(hi.SWEEP_SIGMAS, hi.SWEEP_MS, text_bytes=args.n, seed=21, path=hc.HC_TUNE_SINGLE)
+        tuner.calibrate(sigmas, sorted({m for _, m in grid}), text_bytes=args.n, seed=21,
+                        path=hc.HC_TUNE_SINGLE)
         torch.cuda.synchronize(dev)
         tune_s = time.perf_counter() - t0
 
     # ---- inputs
-    texts_np = {s: hi.sweep_text(s, args.n) for s in hi.SWEEP_SIGMAS}
+    texts_np = {s: hi.sweep_text(s, args.n) for s in sigmas}
     texts = {s: torch.from_numpy(t).to(dev) for s, t in texts_np.items()}
 
     def make_cells(kind):
         out = {}
-        for s in hi.SWEEP_SIGMAS:
-            for m in hi.SWEEP_MS:
-                pats = hi.sweep_patterns(texts_np[s], s, m, args.patterns)
-                opts = None
-                if kind == "tuned":
-                    e = tuner.lookup(s, m)
-                    q, alpha = e["q"], e["alpha"]
-                    opts = hc.SearchOpts(lane_bytes=e["lane_bytes"], mode=e["mode"])
-                else:
-                    q, alpha = hi.paper_q_alpha(s, m)
-                filters = []
-                for x in pats:
-                    f = hc.hc_preprocess(x, q, alpha)
-                    f.to_device()
-                    filters.append(f)
-                out[(s, m)] = (pats, filters, q, alpha, opts)
+        for s, m in grid:
+            pats = hi.sweep_patterns(texts_np[s], s, m, args.patterns)
+            opts = None
+            if kind == "tuned":
+                e = tuner.lookup(s, m)
+                q, alpha = e["q"], e["alpha"]
+                opts = hc.SearchOpts(lane_bytes=e["lane_bytes"], mode=e["mode"])
+            else:
+                q, alpha = hi.paper_q_alpha(s, m)
+            filters = []
+            for x in pats:
+                f = hc.hc_preprocess(x, q, alpha)
+                f.to_device()
+                filters.append(f)
+            out[(s, m)] = (pats, filters, q, alpha, opts)
         return out
 
     cells = make_cells(args.params)
@@ -340,11 +348,13 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     sampler.start()
     t_wall = time.perf_counter()
+    torch.cuda.nvtx.range_push("hc_timed_steps")   # profilers can select the timed region
     for k in range(args.steps):
         step_ev[k][0].record(stream)
         with torch.cuda.stream(stream):
             one_step(cell_ev[k])
         step_ev[k][1].record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
@@ -762,7 +772,7 @@ def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream, dist=None):
         dist.barrier()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        for s in hi.SWEEP_SIGMAS:
+        for s in sorted(pinned):
             n = pinned[s].numel()
             y_dev[:n].copy_(pinned[s], non_blocking=True)
             h2d += n
