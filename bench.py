@@ -62,6 +62,9 @@ def parse_args():
     ap.add_argument("--params", choices=["tuned", "paper"], default="tuned",
                     help="(q, alpha) and launch options per cell: measured by the autotuner on this "
                          "GPU (default), or the paper's Tables 1-3")
+    ap.add_argument("--tuner-table", default="",
+                    help="load the autotuner's table from this file if it exists, else calibrate "
+                         "and save it there (so that two runs use the same parameters)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -276,9 +279,14 @@ def run_gpu(args, rank, world, local_rank):
     if args.params == "tuned":
         tuner = hc.HCTuner()
         t0 = time.perf_counter()
-        tuner.calibrate(sigmas, sorted({m for _, m in grid}), text_bytes=args.n, seed=21,
-                        path=hc.HC_TUNE_SINGLE)
-        torch.cuda.synchronize(dev)
+        if args.tuner_table and os.path.exists(args.tuner_table):
+            tuner.load(args.tuner_table)
+        else:
+            tuner.calibrate(sigmas, sorted({m for _, m in grid}), text_bytes=args.n, seed=21,
+                            path=hc.HC_TUNE_SINGLE)
+            torch.cuda.synchronize(dev)
+            if args.tuner_table:
+                tuner.save(args.tuner_table)
         tune_s = time.perf_counter() - t0
 
     # ---- inputs
