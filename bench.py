@@ -171,21 +171,28 @@ def scan_family(m: int, q: int, mode: int = 0) -> str:
     return "scan_staged"
 
 
+KERNEL_SOURCES = ("paper_2310_15711_gb300/csrc/hc_kernels.cuh", "paper_2310_15711_gb300/csrc/hc_search.cu",
+                  "paper_2310_15711_gb300/csrc/hc_device.cuh")
+
+
 def recorded_traffic(family: str):
-    """DRAM bytes per launch of a kernel family from the committed ncu summary
-    (profiles/traffic.json), if it was taken on the current kernel source."""
+    """DRAM bytes per launch of a kernel family from the committed ncu record
+    (profiles/traffic.json): None unless it was taken on the current kernel
+    sources.  Returns (bytes per launch, record)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2310_15711_gb300", "csrc", "hc_search.cu")
     if not os.path.exists(path):
-        return None
+        return None, None
     with open(path) as f:
         rec = json.load(f)
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, name), "rb") as f:
+            h.update(f.read())
     ent = rec.get(family)
-    if not ent or ent.get("source_sha") != sha:
-        return None
-    return ent.get("dram_bytes_per_launch")
+    if not ent or rec.get("source_sha") != h.hexdigest()[:16]:
+        return None, None
+    return ent.get("dram_bytes_per_launch"), ent
 
 
 def measured_peaks():
@@ -435,7 +442,7 @@ def run_gpu(args, rank, world, local_rank):
     dom_ms, dom_launches = kernel_times[dominant]
     achieved = fam_bytes.get(dominant, 0.0) * args.steps / (dom_ms / 1e3) / GB if dom_ms else 0.0
     peak, peak_kind = measured_peaks()
-    traffic = recorded_traffic(dominant)
+    traffic, traffic_rec = recorded_traffic(dominant)
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
@@ -448,7 +455,11 @@ def run_gpu(args, rank, world, local_rank):
                      "avg_launch_us": round(dom_ms * 1e3 / max(dom_launches, 1), 2),
                      "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "kernel_timing": "library CUDA events on the launching stream, over the same "
-                                      "steps run again right after the timed region"},
+                                      "steps run again right after the timed region",
+                     "traffic_case": (None if traffic_rec is None else
+                                      {"case": traffic_rec["case"],
+                                       "algorithmic_bytes": traffic_rec["algorithmic_bytes_per_launch"],
+                                       "summary": traffic_rec["summary"]})},
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in kernel_times.items() if v[1]},
         "gpu_launches": int(launches),
         "clocks": clocks,
