@@ -51,12 +51,12 @@ __device__ __forceinline__ uint32_t pattern_hash(const uint8_t* x, int i, int q,
 }
 
 __global__ void __launch_bounds__(kThreads)
-    hc_batch_preprocess_kernel(SearchArgs* args, unsigned long long* counter) {
+    hc_batch_preprocess_kernel(SearchArgs* args, unsigned long long* counters) {
   extern __shared__ __align__(128) uint8_t smem[];
   pdl_launch_dependents();  // the scan kernel may be scheduled; it waits for this grid
   uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
   const int tid = threadIdx.x;
-  if (blockIdx.x == 0 && tid == 0) *counter = 0;
+  if (blockIdx.x == 0 && tid < kMaxScanClasses) counters[tid] = 0;
   SearchArgs* a = args + blockIdx.x;
   if (a->records == 0) {  // n < m: no window
     if (tid == 0) *a->count_out = 0;
@@ -314,15 +314,47 @@ int plan_add_query(BatchPlan& plan, const hc_batch_query& Q, size_t i, const Que
   return HC_OK;
 }
 
+namespace {
+
+size_t scan_smem(const BatchLayout& lay) {
+  return size_t((lay.f_bytes + 15u) & ~15u) + lay.x_bytes + size_t(kSlots) * kThreads * 4 +
+         size_t(kWarps) * lay.ring_bytes;
+}
+
+}  // namespace
+
 int plan_finish(BatchPlan& plan, int dev, const char* who) {
   const DeviceInfo& di = device_info(dev);
   plan.lay.f_bytes = (plan.lay.f_bytes + 15u) & ~15u;
   plan.smem_pre = std::max<size_t>(plan.lay.f_bytes, 16);
-  plan.smem_scan = size_t(plan.lay.f_bytes) + plan.lay.x_bytes + size_t(kSlots) * kThreads * 4 +
-                   size_t(kWarps) * plan.lay.ring_bytes;
+  plan.smem_scan = scan_smem(plan.lay);
   plan.smem_emit = size_t(plan.lay.f_bytes) + size_t(kSlots) * kThreads * 4;
-  if (plan.smem_scan + 2048 > di.smem_optin)
-    return set_error(HC_ERR_ARG, std::string(who) + ": filter and staging buffers exceed shared memory");
+  // class of a query: resident CTAs per SM its own layout allows (1 .. 4),
+  // estimated from the SM's shared memory (with a reserve per CTA)
+  const size_t per_sm = 233472;
+  std::vector<int> qclass(plan.args.size(), 0);
+  plan.classes.assign(kMaxScanClasses, ScanClass{});
+  for (size_t i = 0; i < plan.args.size(); ++i) {
+    const SearchArgs& a = plan.args[i];
+    BatchLayout l{(a.fwords * 4u + 15u) & ~15u, a.x_smem, static_cast<uint32_t>(a.stages) * a.stage_bytes};
+    const size_t need = scan_smem(l);
+    if (need + 2048 > di.smem_optin)
+      return set_error(HC_ERR_ARG, std::string(who) + ": filter and staging buffers exceed shared memory");
+    const int ctas = static_cast<int>(std::min<size_t>(kMaxScanClasses, std::max<size_t>(1, per_sm / (need + 1536))));
+    qclass[i] = kMaxScanClasses - ctas;  // class 0: the highest occupancy
+    BatchLayout& cl = plan.classes[qclass[i]].lay;
+    cl = {std::max(cl.f_bytes, l.f_bytes), std::max(cl.x_bytes, l.x_bytes), std::max(cl.ring_bytes, l.ring_bytes)};
+  }
+  std::stable_sort(plan.tiles.begin(), plan.tiles.end(),
+                   [&](const BatchTile& x, const BatchTile& y) { return qclass[x.query] < qclass[y.query]; });
+  unsigned long long begin = 0;
+  for (int c = 0; c < kMaxScanClasses; ++c) {
+    ScanClass& sc = plan.classes[c];
+    sc.tile_begin = begin;
+    while (begin < plan.tiles.size() && qclass[plan.tiles[begin].query] == c) ++begin;
+    sc.ntiles = begin - sc.tile_begin;
+    sc.smem = scan_smem(sc.lay);
+  }
   return init_batch_kernels(dev);
 }
 
@@ -337,54 +369,87 @@ void plan_bind(BatchPlan& plan, uint32_t* d_filters, uint8_t* d_ws) {
   }
 }
 
-int batch_grid(const BatchPlan& plan, int dev, int* grid) {
+namespace {
+
+int class_grid(size_t smem, unsigned long long ntiles, int dev, int* grid) {
   static std::mutex mu;
   static std::vector<std::pair<std::pair<int, size_t>, int>> cache;  // (dev, smem) -> CTAs per SM
   int per_sm = -1;
   {
     std::lock_guard<std::mutex> lock(mu);
     for (auto& c : cache)
-      if (c.first.first == dev && c.first.second == plan.smem_scan) per_sm = c.second;
+      if (c.first.first == dev && c.first.second == smem) per_sm = c.second;
   }
   if (per_sm < 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hc_batch_scan_kernel, kThreads,
-                                                                  plan.smem_scan);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hc_batch_scan_kernel, kThreads, smem);
     if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(batch)");
     std::lock_guard<std::mutex> lock(mu);
-    if (cache.size() < 256) cache.push_back({{dev, plan.smem_scan}, per_sm});
+    if (cache.size() < 256) cache.push_back({{dev, smem}, per_sm});
   }
   const DeviceInfo& di = device_info(dev);
   *grid = static_cast<int>(std::min<unsigned long long>(
-      static_cast<unsigned long long>(std::max(per_sm, 1)) * di.sm_count,
-      std::max<unsigned long long>(plan.tiles.size(), 1)));
+      static_cast<unsigned long long>(std::max(per_sm, 1)) * di.sm_count, std::max<unsigned long long>(ntiles, 1)));
   return HC_OK;
+}
+
+}  // namespace
+
+int batch_grids(BatchPlan& plan, int dev) {
+  for (ScanClass& c : plan.classes)
+    if (c.ntiles > 0) {
+      int rc = class_grid(c.smem, c.ntiles, dev, &c.grid);
+      if (rc != HC_OK) return rc;
+    }
+  return HC_OK;
+}
+
+BatchLaunch make_launch(const BatchPlan& plan, const SearchArgs* args, const BatchTile* tiles,
+                        const EmitTile* etiles, unsigned long long* counters) {
+  BatchLaunch L;
+  L.args = args;
+  L.tiles = tiles;
+  L.etiles = etiles;
+  L.counters = counters;
+  L.nq = plan.args.size();
+  L.netiles = plan.etiles.size();
+  L.smem_pre = plan.smem_pre;
+  L.smem_emit = plan.smem_emit;
+  for (const ScanClass& c : plan.classes)
+    if (c.ntiles > 0 && L.nclasses < kMaxScanClasses) L.classes[L.nclasses++] = c;
+  return L;
 }
 
 int launch_batch(const BatchLaunch& L, cudaStream_t stream) {
   if (L.nq == 0) return HC_OK;
   TimingToken t0 = timing_begin(kKindPreprocess, stream);
   hc_batch_preprocess_kernel<<<static_cast<unsigned>(L.nq), kThreads, L.smem_pre, stream>>>(
-      const_cast<SearchArgs*>(L.args), L.counter);
+      const_cast<SearchArgs*>(L.args), L.counters);
   cudaError_t e = cudaGetLastError();
   timing_end(t0, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_batch_preprocess_kernel launch");
-  if (L.ntiles == 0) {
+  if (L.nclasses == 0) {
     g_launches.fetch_add(1);
     return HC_OK;
   }
-  TimingToken t1 = timing_begin(kKindBatch, stream);
-  e = launch_dependent(hc_batch_scan_kernel, static_cast<unsigned>(L.grid_scan), kThreads, L.smem_scan, stream,
-                       !t1.active() && !t0.active(), L.args, L.tiles, L.ntiles, L.counter, L.lay);
-  if (e == cudaSuccess) e = cudaGetLastError();
-  timing_end(t1, stream);
-  if (e != cudaSuccess) return cuda_error(e, "hc_batch_scan_kernel launch");
+  bool prev_timed = t0.active();
+  for (int c = 0; c < L.nclasses; ++c) {
+    const ScanClass& sc = L.classes[c];
+    TimingToken t1 = timing_begin(kKindBatch, stream);
+    e = launch_dependent(hc_batch_scan_kernel, static_cast<unsigned>(sc.grid), kThreads, sc.smem, stream,
+                         !t1.active() && !prev_timed, L.args, L.tiles + sc.tile_begin, sc.ntiles,
+                         L.counters + c, sc.lay);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    timing_end(t1, stream);
+    prev_timed = t1.active();
+    if (e != cudaSuccess) return cuda_error(e, "hc_batch_scan_kernel launch");
+  }
   TimingToken t2 = timing_begin(kKindEmit, stream);
   e = launch_dependent(hc_batch_emit_kernel, static_cast<unsigned>(L.netiles * kEmitSplit), kThreads, L.smem_emit,
                        stream, !t2.active(), L.args, L.etiles);
   if (e == cudaSuccess) e = cudaGetLastError();
   timing_end(t2, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_batch_emit_kernel launch");
-  g_launches.fetch_add(3);
+  g_launches.fetch_add(2 + static_cast<uint64_t>(L.nclasses));
   return HC_OK;
 }
 
@@ -537,7 +602,7 @@ int create_batch(const hc_batch_query* qs, size_t nq, const hc_tuner* tuner, hc_
   if (rc == HC_OK) rc = dev_alloc(&b->d_args, nq, "cudaMalloc(batch args)");
   if (rc == HC_OK) rc = dev_alloc(&b->d_tiles, plan.tiles.size(), "cudaMalloc(batch tiles)");
   if (rc == HC_OK) rc = dev_alloc(&b->d_etiles, plan.etiles.size(), "cudaMalloc(batch emit tiles)");
-  if (rc == HC_OK) rc = dev_alloc(&b->d_counter, 1, "cudaMalloc(batch counter)");
+  if (rc == HC_OK) rc = dev_alloc(&b->d_counter, kMaxScanClasses, "cudaMalloc(batch counters)");
   if (rc == HC_OK) rc = dev_alloc(&b->d_filters, plan.filter_words, "cudaMalloc(batch filters)");
   if (rc == HC_OK) rc = dev_alloc(&b->d_ws, plan.ws_bytes, "cudaMalloc(batch workspace)");
   if (rc != HC_OK) {
@@ -556,23 +621,12 @@ int create_batch(const hc_batch_query* qs, size_t nq, const hc_tuner* tuner, hc_
     delete b;
     return cuda_error(e, "cudaMemcpy(batch tables)");
   }
-  BatchLaunch& L = b->launch;
-  L.args = b->d_args;
-  L.tiles = b->d_tiles;
-  L.etiles = b->d_etiles;
-  L.counter = b->d_counter;
-  L.nq = nq;
-  L.ntiles = plan.tiles.size();
-  L.netiles = plan.etiles.size();
-  L.lay = plan.lay;
-  L.smem_pre = plan.smem_pre;
-  L.smem_scan = plan.smem_scan;
-  L.smem_emit = plan.smem_emit;
-  rc = batch_grid(plan, dev, &L.grid_scan);
+  rc = batch_grids(plan, dev);
   if (rc != HC_OK) {
     delete b;
     return rc;
   }
+  b->launch = make_launch(plan, b->d_args, b->d_tiles, b->d_etiles, b->d_counter);
   *out = reinterpret_cast<hc_batch*>(b);
   return HC_OK;
 }

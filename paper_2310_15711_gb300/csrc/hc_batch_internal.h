@@ -41,8 +41,23 @@ struct QueryParams {
   int q = 0, alpha = 0, lane_bytes = 0, mode = 0;
 };
 
+// Queries are grouped by the number of CTAs per SM their own shared-memory
+// layout allows (filter, pattern and staging ring differ per query); each
+// group runs as one persistent scan whose layout is the group's largest, so
+// one query with a large filter or ring does not lower the occupancy of the
+// whole batch.
+constexpr int kMaxScanClasses = 4;
+
+struct ScanClass {
+  unsigned long long tile_begin = 0, ntiles = 0;  // its tiles: tiles[tile_begin ..)
+  BatchLayout lay{};
+  size_t smem = 0;  // dynamic shared memory of its scan launch
+  int grid = 0;     // persistent grid of its scan launch
+};
+
 struct BatchPlan {
   std::vector<SearchArgs> args;
+  std::vector<ScanClass> classes;  // set by plan_finish; tiles are sorted by class
   std::vector<QueryParams> params;
   std::vector<BatchTile> tiles;
   std::vector<EmitTile> etiles;
@@ -65,8 +80,9 @@ unsigned long long record_bytes_for(unsigned long long total_text, int dev);
 // Checks pointers, alignment and parameter ranges; reads no device memory.
 int plan_add_query(BatchPlan& plan, const hc_batch_query& Q, size_t i, const QueryParams& p,
                    unsigned long long record_bytes, const char* who);
-// Shared-memory layout of the plan; HC_ERR_ARG when the largest query's
-// filter and staging buffers do not fit in one CTA.
+// Scan classes (tiles sorted by class, each class's layout, shared memory
+// and grid) and the emit layout; HC_ERR_ARG when a query's filter and
+// staging buffers do not fit in one CTA.
 int plan_finish(BatchPlan& plan, int dev, const char* who);
 // Writes the device addresses of the filter area (filter_words words) and
 // the workspace area (ws_bytes bytes, 16-byte aligned) into the arguments.
@@ -75,19 +91,24 @@ void plan_bind(BatchPlan& plan, uint32_t* d_filters, uint8_t* d_ws);
 // Everything one run of a planned batch needs on the device.
 struct BatchLaunch {
   const SearchArgs* args = nullptr;  // nq arguments
-  const BatchTile* tiles = nullptr;
+  const BatchTile* tiles = nullptr;  // sorted by scan class
   const EmitTile* etiles = nullptr;
-  unsigned long long* counter = nullptr;  // work counter of the scan (reset by the run)
+  unsigned long long* counters = nullptr;  // kMaxScanClasses work counters (reset by the run)
   size_t nq = 0;
-  unsigned long long ntiles = 0, netiles = 0;
-  BatchLayout lay{};
-  size_t smem_pre = 0, smem_scan = 0, smem_emit = 0;
-  int grid_scan = 0;
+  unsigned long long netiles = 0;
+  ScanClass classes[kMaxScanClasses];
+  int nclasses = 0;
+  size_t smem_pre = 0, smem_emit = 0;
 };
 
-// Persistent scan grid for a plan on device dev (SMs x resident CTAs, at
+// Persistent grid of each scan class on device dev (SMs x resident CTAs, at
 // most one CTA per tile).
-int batch_grid(const BatchPlan& plan, int dev, int* grid);
+int batch_grids(BatchPlan& plan, int dev);
+
+// The launch description of a plan whose tables are at the given device
+// addresses (counters: kMaxScanClasses of them).
+BatchLaunch make_launch(const BatchPlan& plan, const SearchArgs* args, const BatchTile* tiles,
+                        const EmitTile* etiles, unsigned long long* counters);
 // Enqueues preprocessing, scan and emit on `stream`; allocates nothing and
 // is graph-capturable.  Counts its launches.
 int launch_batch(const BatchLaunch& L, cudaStream_t stream);

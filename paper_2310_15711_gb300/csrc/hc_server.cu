@@ -308,8 +308,7 @@ int Server::launch_batched(Slot& s, const std::vector<size_t>& which) {
     xbytes += align_up(r->x.size(), 16);
   }
   if (rc == HC_OK) rc = plan_finish(plan, dev, "hc_server");
-  BatchLaunch L;
-  if (rc == HC_OK) rc = batch_grid(plan, dev, &L.grid_scan);
+  if (rc == HC_OK) rc = batch_grids(plan, dev);
   if (rc != HC_OK) return rc;
   const size_t o_args = kAlign;
   const size_t o_tiles = o_args + align_up(nq * sizeof(SearchArgs));
@@ -338,17 +337,10 @@ int Server::launch_batched(Slot& s, const std::vector<size_t>& which) {
   e = cudaMemcpyAsync(d + o_args, s.stage + o_args, table_end - o_args, cudaMemcpyHostToDevice, s.stream);
   if (e != cudaSuccess) rc = cuda_error(e, "cudaMemcpyAsync(server tables)");
   if (rc == HC_OK) {
-    L.args = reinterpret_cast<const SearchArgs*>(d + o_args);
-    L.tiles = reinterpret_cast<const BatchTile*>(d + o_tiles);
-    L.etiles = reinterpret_cast<const EmitTile*>(d + o_etiles);
-    L.counter = reinterpret_cast<unsigned long long*>(d);
-    L.nq = nq;
-    L.ntiles = plan.tiles.size();
-    L.netiles = plan.etiles.size();
-    L.lay = plan.lay;
-    L.smem_pre = plan.smem_pre;
-    L.smem_scan = plan.smem_scan;
-    L.smem_emit = plan.smem_emit;
+    const BatchLaunch L = make_launch(plan, reinterpret_cast<const SearchArgs*>(d + o_args),
+                                      reinterpret_cast<const BatchTile*>(d + o_tiles),
+                                      reinterpret_cast<const EmitTile*>(d + o_etiles),
+                                      reinterpret_cast<unsigned long long*>(d));  // kAlign bytes of counters
     rc = launch_batch(L, s.stream);
   }
   cudaFreeAsync(blk, s.stream);  // after the kernels, in stream order

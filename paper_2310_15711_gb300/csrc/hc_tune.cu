@@ -119,7 +119,7 @@ struct Scratch {
   size_t tiles_cap = 0;
   EmitTile* etiles = nullptr;
   size_t etiles_cap = 0;
-  unsigned long long* counter = nullptr;  // [0] work counter, [1] count
+  unsigned long long* counter = nullptr;  // [0, kMaxScanClasses) work counters, then the count
   uint32_t* filters = nullptr;
   size_t filters_cap = 0;
   uint8_t* ws = nullptr;
@@ -182,7 +182,7 @@ int time_candidate(Scratch& sc, int dev, const uint8_t* x, uint64_t m, const uin
   Q.n = n;
   Q.q = p.q;
   Q.alpha = p.alpha;
-  Q.count_dev = reinterpret_cast<uint64_t*>(sc.counter + 1);
+  Q.count_dev = reinterpret_cast<uint64_t*>(sc.counter + kMaxScanClasses);
   Q.lane_bytes = p.lane_bytes;
   Q.mode = p.mode;
   BatchPlan plan;
@@ -211,20 +211,9 @@ int time_candidate(Scratch& sc, int dev, const uint8_t* x, uint64_t m, const uin
   if (e == cudaSuccess && eb)
     e = cudaMemcpyAsync(sc.etiles, sc.host + sizeof(SearchArgs) + tb, eb, cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync(tuner tables)");
-  BatchLaunch L;
-  L.args = sc.args;
-  L.tiles = sc.tiles;
-  L.etiles = sc.etiles;
-  L.counter = sc.counter;
-  L.nq = 1;
-  L.ntiles = plan.tiles.size();
-  L.netiles = plan.etiles.size();
-  L.lay = plan.lay;
-  L.smem_pre = plan.smem_pre;
-  L.smem_scan = plan.smem_scan;
-  L.smem_emit = plan.smem_emit;
-  rc = batch_grid(plan, dev, &L.grid_scan);
+  rc = batch_grids(plan, dev);
   if (rc != HC_OK) return rc;
+  const BatchLaunch L = make_launch(plan, sc.args, sc.tiles, sc.etiles, sc.counter);
   if (warm) rc = launch_batch(L, stream);
   double best = INFINITY;
   for (int r = 0; r < reps && rc == HC_OK; ++r) {
@@ -280,7 +269,7 @@ int time_candidate_single(Scratch& sc, int dev, const std::vector<uint8_t>& xh, 
   }
   const uint32_t* F_dev = reinterpret_cast<const uint32_t*>(sc.fx);
   const uint8_t* x_dev = sc.fx + fbytes;
-  uint64_t* count = reinterpret_cast<uint64_t*>(sc.counter + 1);
+  uint64_t* count = reinterpret_cast<uint64_t*>(sc.counter + kMaxScanClasses);
   if (rc == HC_OK && warm) rc = launch_planned_filter_ptrs(f, sp, F_dev, x_dev, y, n, nullptr, 0, count, sc.ws, stream);
   double best = INFINITY;
   for (int r = 0; r < reps && rc == HC_OK; ++r) {
@@ -488,7 +477,7 @@ int hc_tuner_calibrate(hc_tuner* tp, const int* sigmas, size_t nsigma, const uin
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = HC_OK;
   e = cudaMalloc(&sc.args, sizeof(SearchArgs));
-  if (e == cudaSuccess) e = cudaMalloc(&sc.counter, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&sc.counter, (kMaxScanClasses + 1) * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) rc = cuda_error(e, "hc_tuner_calibrate setup");
