@@ -342,8 +342,18 @@ int plan_finish(BatchPlan& plan, int dev, const char* who) {
       return set_error(HC_ERR_ARG, std::string(who) + ": filter and staging buffers exceed shared memory");
     const int ctas = static_cast<int>(std::min<size_t>(kMaxScanClasses, std::max<size_t>(1, per_sm / (need + 1536))));
     qclass[i] = kMaxScanClasses - ctas;  // class 0: the highest occupancy
+  }
+  // a batch whose tiles fit in one wave even at its lowest occupancy runs as
+  // one class (one launch fewer per class saved; occupancy does not matter)
+  int lowest = 0;
+  for (int c : qclass) lowest = std::max(lowest, c);
+  if (plan.tiles.size() <= static_cast<size_t>(kMaxScanClasses - lowest) * di.sm_count)
+    std::fill(qclass.begin(), qclass.end(), lowest);
+  for (size_t i = 0; i < plan.args.size(); ++i) {
+    const SearchArgs& a = plan.args[i];
     BatchLayout& cl = plan.classes[qclass[i]].lay;
-    cl = {std::max(cl.f_bytes, l.f_bytes), std::max(cl.x_bytes, l.x_bytes), std::max(cl.ring_bytes, l.ring_bytes)};
+    cl = {std::max(cl.f_bytes, (a.fwords * 4u + 15u) & ~15u), std::max(cl.x_bytes, a.x_smem),
+          std::max(cl.ring_bytes, static_cast<uint32_t>(a.stages) * a.stage_bytes)};
   }
   std::stable_sort(plan.tiles.begin(), plan.tiles.end(),
                    [&](const BatchTile& x, const BatchTile& y) { return qclass[x.query] < qclass[y.query]; });
