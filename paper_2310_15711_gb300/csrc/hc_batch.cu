@@ -41,6 +41,7 @@ constexpr unsigned long long kTileTextBytes = 64ull << 10;  // text per record, 
 // overflows are re-scanned by the emit kernel, so the floor keeps dense
 // queries with a small cap from re-scanning most of their records.
 constexpr unsigned long long kMinSpill = 1ull << 15;
+constexpr size_t kOneClassQueries = 32;  // batches up to this size run one scan class
 
 // h(x[i .. i+q-1]) by Horner's rule from the last byte down (Eq. 3, Eq. 4).
 __device__ __forceinline__ uint32_t pattern_hash(const uint8_t* x, int i, int q, int s,
@@ -343,11 +344,13 @@ int plan_finish(BatchPlan& plan, int dev, const char* who) {
     const int ctas = static_cast<int>(std::min<size_t>(kMaxScanClasses, std::max<size_t>(1, per_sm / (need + 1536))));
     qclass[i] = kMaxScanClasses - ctas;  // class 0: the highest occupancy
   }
-  // a batch whose tiles fit in one wave even at its lowest occupancy runs as
-  // one class (one launch fewer per class saved; occupancy does not matter)
+  // a small batch, or one whose tiles fit in one wave even at its lowest
+  // occupancy, runs as one class: the class scans of a batch run one after
+  // another, which would add up the latencies of its few queries
   int lowest = 0;
   for (int c : qclass) lowest = std::max(lowest, c);
-  if (plan.tiles.size() <= static_cast<size_t>(kMaxScanClasses - lowest) * di.sm_count)
+  if (plan.args.size() <= kOneClassQueries ||
+      plan.tiles.size() <= static_cast<size_t>(kMaxScanClasses - lowest) * di.sm_count)
     std::fill(qclass.begin(), qclass.end(), lowest);
   for (size_t i = 0; i < plan.args.size(); ++i) {
     const SearchArgs& a = plan.args[i];
