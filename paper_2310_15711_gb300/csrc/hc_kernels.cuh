@@ -19,9 +19,10 @@ constexpr int kSlots = 2;
 constexpr int kMaxSmemX = 4096;             // larger patterns verify from global memory
 constexpr size_t kMaxStagedM = 16384;       // larger patterns use the unstaged kernel
 constexpr unsigned long long kNoOverflow = ~0ull;
-constexpr int kDirectShift = 200;
+constexpr int kDirectShift = 200;           // shifts this long skip most 32-byte sectors
 constexpr int kEmitSplit = 2;               // CTAs of the emit kernel per record group
-constexpr int kMaxEmitGroup = 64;           // records per emit record group, at most           // shifts this long skip most 32-byte sectors
+constexpr int kMaxEmitGroup = 64;           // records per emit record group, at most
+constexpr int kEmitUnits = 8;               // 8-byte region loads in flight per emit thread
 
 
 // Bytes of one staging buffer: head (< 16) + C + m - 1 bytes of text rounded
@@ -541,54 +542,79 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
     s_ovf[tid] = a.cta_overflow[r0 + tid];
   }
   __syncthreads();
-  unsigned long long P = 0;  // output offset of record b (updated below)
-  for (int w = 0; w < kWarps; ++w) P += red[w];
+  // per record of the group: output offset P, positions to copy, and the
+  // prefix of 2-position units, so that the whole group is copied in one
+  // pass (no per-record latency chain)
+  __shared__ unsigned long long s_P[kMaxEmitGroup + 1], s_U[kMaxEmitGroup + 1], s_N[kMaxEmitGroup];
+  const int nrec = static_cast<int>(r1 - r0);
+  if (tid == 0) {
+    unsigned long long P = 0, U = 0;
+    for (int w = 0; w < kWarps; ++w) P += red[w];
+    for (int k = 0; k < nrec; ++k) {
+      const unsigned long long T = s_tot[k], ovf = s_ovf[k];
+      const unsigned long long stored = ovf == kNoOverflow ? T : (ovf & ((1ull << 40) - 1));
+      const unsigned long long ncopy = a.cap > P ? min(stored, a.cap - P) : 0ull;
+      s_P[k] = P;
+      s_U[k] = U;
+      s_N[k] = ncopy;
+      U += (ncopy + 1) / 2;
+      P += T;
+    }
+    s_P[nrec] = P;
+    s_U[nrec] = U;
+    if (part == 0 && r1 == a.records) *a.count_out = P;
+  }
+  __syncthreads();
+  {
+    // unit u of record k: region entries 2(u - U_k) and +1 (8-byte loads;
+    // regions are 16-byte aligned); consecutive threads take consecutive
+    // units, so a warp's 16-byte stores cover 512 contiguous bytes; 16-byte
+    // stores where the output address is 16-byte aligned
+    const unsigned long long U = s_U[nrec];
+    const unsigned long long stride = static_cast<unsigned long long>(kThreads) * kEmitSplit;
+    int rk = 0;  // record of this thread's current unit (units only increase)
+    for (unsigned long long u0 = part * kThreads + tid; u0 < U; u0 += kEmitUnits * stride) {
+      uint2 v[kEmitUnits];
+      int rec[kEmitUnits];
+#pragma unroll
+      for (int uu = 0; uu < kEmitUnits; ++uu) {
+        const unsigned long long u = u0 + static_cast<unsigned long long>(uu) * stride;
+        rec[uu] = -1;
+        if (u < U) {
+          while (s_U[rk + 1] <= u) ++rk;
+          rec[uu] = rk;
+          const uint2* r2 = reinterpret_cast<const uint2*>(a.region + (r0 + rk) * a.region_entries);
+          v[uu] = __ldcs(r2 + (u - s_U[rk]));
+        }
+      }
+#pragma unroll
+      for (int uu = 0; uu < kEmitUnits; ++uu) {
+        if (rec[uu] < 0) continue;
+        const int k = rec[uu];
+        const unsigned long long u = u0 + static_cast<unsigned long long>(uu) * stride;
+        const unsigned long long e = (u - s_U[k]) * 2;   // first entry of the unit
+        const unsigned long long vbase = (r0 + k) * a.chunks_per_cta * a.C;
+        unsigned long long* o = a.pos + s_P[k] + e;
+        if (e + 2 <= s_N[k] && (reinterpret_cast<uintptr_t>(o) & 15u) == 0u) {
+          *reinterpret_cast<ulonglong2*>(o) = make_ulonglong2(vbase + v[uu].x, vbase + v[uu].y);
+        } else {
+          o[0] = vbase + v[uu].x;
+          if (e + 1 < s_N[k]) o[1] = vbase + v[uu].y;
+        }
+      }
+    }
+  }
 
   bool f_loaded = false;
   for (unsigned long long b = r0; b < r1; ++b) {
     const unsigned long long T = s_tot[b - r0];
     const unsigned long long ovf = s_ovf[b - r0];
-    if (part == 0 && b == a.records - 1 && tid == 0) *a.count_out = P + T;
-    if (T == 0) continue;  // nothing to copy, nothing overflowed
-    const unsigned long long stored = ovf == kNoOverflow ? T : (ovf & ((1ull << 40) - 1));
+    const unsigned long long P = s_P[b - r0];
+    if (ovf == kNoOverflow || T == 0) continue;  // nothing to re-scan
+    const unsigned long long stored = ovf & ((1ull << 40) - 1);
     const unsigned long long c0 = b * a.chunks_per_cta;
-    const unsigned long long vbase = c0 * a.C;
-    const uint32_t* region = a.region + b * a.region_entries;
-    // copy: 16-byte region loads (regions are 16-byte aligned), four of them
-    // in flight per thread; 16-byte stores when the output offset is even
-    const unsigned long long ncopy = a.cap > P ? min(stored, a.cap - P) : 0ull;
-    const uint4* r4 = reinterpret_cast<const uint4*>(region);
-    const unsigned long long nvec = (ncopy + 3) / 4;
-    const unsigned long long stride = static_cast<unsigned long long>(kThreads) * kEmitSplit;
-    // 16-byte stores only where the output address itself is 16-byte aligned
-    // (k is a multiple of 4, so a.pos + P + k is aligned iff a.pos + P is)
-    const bool even = (reinterpret_cast<uintptr_t>(a.pos + P) & 15u) == 0u;
-    for (unsigned long long k0 = part * kThreads + tid; k0 < nvec; k0 += 4 * stride) {
-      uint4 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const unsigned long long k = k0 + static_cast<unsigned long long>(u) * stride;
-        if (k < nvec) v[u] = __ldcs(r4 + k);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const unsigned long long k = (k0 + static_cast<unsigned long long>(u) * stride) * 4;
-        if (k < ncopy) {
-          unsigned long long* o = a.pos + P + k;
-          if (even && k + 4 <= ncopy) {
-            __stcs(reinterpret_cast<ulonglong2*>(o), make_ulonglong2(vbase + v[u].x, vbase + v[u].y));
-            __stcs(reinterpret_cast<ulonglong2*>(o + 2), make_ulonglong2(vbase + v[u].z, vbase + v[u].w));
-          } else {
-            __stcs(o, vbase + v[u].x);
-            if (k + 1 < ncopy) __stcs(o + 1, vbase + v[u].y);
-            if (k + 2 < ncopy) __stcs(o + 2, vbase + v[u].z);
-            if (k + 3 < ncopy) __stcs(o + 3, vbase + v[u].w);
-          }
-        }
-      }
-    }
     if (part == 0) {
-      if (ovf != kNoOverflow && P + stored < a.cap) {
+      if (P + stored < a.cap) {
         // re-scan the chunks from the first unstored one on
         uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
         uint32_t* slots = Fs + ((a.fwords + 3u) & ~3u);
@@ -632,7 +658,6 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
         }
       }
     }
-    P += T;
   }
 }
 
