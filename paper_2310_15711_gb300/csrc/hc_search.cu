@@ -384,7 +384,7 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   if (L < 1 || L > 4096) return set_error(HC_ERR_ARG, "hc_search: lane_bytes out of [1, 4096]");
   if (kind == HC_MODE_DENSE && L > 256)
     return set_error(HC_ERR_ARG, "hc_search: the dense mode needs lane_bytes <= 256");
-  const int stages = o && o->stages ? o->stages : (kind == HC_MODE_STAGED ? 2 : 3);
+  const int stages = o && o->stages ? o->stages : (kind == HC_MODE_DIRECT ? 3 : 2);
   if (stages < 2 || stages > kMaxStages) return set_error(HC_ERR_ARG, "hc_search: stages out of [2, 4]");
   p.kind = kind;
   p.L = L;
