@@ -177,7 +177,8 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
     // masked
     for (int base = -a.head; base < wins; base += 512) {
       const int w0 = base + 16 * lane;      // first window of this lane
-      uint32_t mbits = 0;
+      uint32_t dg[4] = {~0u, ~0u, ~0u, ~0u};
+      uint32_t cand = 0;
       if (w0 < wins) {  // lanes past the chunk's end read nothing
         const uint32_t o = static_cast<uint32_t>(a.head + w0);
         const uint4 A = *reinterpret_cast<const uint4*>(sb + o);
@@ -193,17 +194,27 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
             const uint32_t col = (cc & 3) ? __funnelshift_r(Tw[wq], Tw[wq + 1], 8u * (cc & 3)) : Tw[wq];
             d |= col ^ xrep[cc];
           }
-          // exact zero-byte test: bit 7 of a byte set iff the byte is 0
-          const uint32_t z = ~(((d & 0x7f7f7f7fu) + 0x7f7f7f7fu) | d | 0x7f7f7f7fu);
-          // gather the four bit-7 flags into bits 4g .. 4g+3
+          dg[g] = d;
+          // nonzero iff d has a zero byte (exact for the word; the flag
+          // positions above a zero byte may be wrong, so they are not used)
+          cand |= (d - 0x01010101u) & ~d & 0x80808080u;
+        }
+        if (!filter_passes) cand = 0;
+      }
+      if (__ballot_sync(0xffffffffu, cand != 0u) == 0u) continue;
+      uint32_t mbits = 0;
+      if (cand != 0u) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          // exact zero-byte test: bit 7 of a byte set iff the byte is 0;
+          // the four flags go to bits 4g .. 4g+3
+          const uint32_t z = ~(((dg[g] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | dg[g] | 0x7f7f7f7fu);
           mbits |= (((z >> 7) & 0x01010101u) * 0x01020408u >> 24) << (4 * g);
         }
         // windows outside [0, wins)
         if (w0 < 0) mbits &= 0xffffu << min(-w0, 16);
         if (w0 + 16 > wins) mbits &= 0xffffu >> (16 - (wins - w0));
-        if (!filter_passes) mbits = 0;
       }
-      if (__ballot_sync(0xffffffffu, mbits != 0u) == 0u) continue;
       // in-order compaction (lanes in order, a lane's windows in order),
       // written straight to the spill region
       const uint32_t mine = static_cast<uint32_t>(__popc(mbits));
