@@ -432,11 +432,17 @@ def run_gpu(args, rank, world, local_rank):
         fam = scan_family(m, q, opts.mode if opts is not None else 0)
         fam_bytes[fam] = fam_bytes.get(fam, 0.0) + n * args.patterns + 4 * occ
         fam_bytes["emit"] = fam_bytes.get("emit", 0.0) + 12 * occ
+        cell_s = cell_ms[ci] / 1e3
+        # algorithmic DRAM bytes of the cell's searches: the text (every byte
+        # is read when the whole text is staged; direct-mode cells read less),
+        # 4 per spilled occurrence, 12 per emitted one (read 4, write 8)
+        alg = (n * args.patterns + 16 * occ) * args.steps
         per_cell[f"s{s}_m{m}"] = {
-            "GBps": round(n * args.patterns * args.steps / (cell_ms[ci] / 1e3) / GB, 1),
+            "GBps": round(n * args.patterns * args.steps / cell_s / GB, 1),
             "kernel": fam, "q": q, "alpha": alpha,
             "lane_bytes": opts.lane_bytes if opts is not None else 0,
             "occ_per_pattern": float(cnt[ci].mean()),
+            "hbm_frac": round(alg / cell_s / GB / measured_peaks()[0], 3) if fam != "scan_direct" else None,
         }
     dominant = max(kernel_times, key=lambda k: kernel_times[k][0])
     dom_ms, dom_launches = kernel_times[dominant]
@@ -466,6 +472,14 @@ def run_gpu(args, rank, world, local_rank):
         "cells": per_cell,
         "wall_s_timed": round(wall, 3),
     }
+    small = [(k, v["hbm_frac"]) for k, v in per_cell.items()
+             if int(k.split("_m")[1]) <= 32 and v["hbm_frac"] is not None]
+    if small:
+        fr = sorted(f for _, f in small)
+        line["m_le_32"] = {"cells": len(fr), "at_or_above_0.60": sum(1 for f in fr if f >= 0.60),
+                           "median_hbm_frac": fr[len(fr) // 2], "min": fr[0], "max": fr[-1],
+                           "note": "per cell: algorithmic bytes of its searches (text + 16 per "
+                                   "occurrence) / its device time, of measured HBM"}
     if paper is not None:
         line["paper_params"] = paper
         line["tune_s"] = round(tune_s, 2)
