@@ -301,6 +301,14 @@ int hc_tuner_save(const hc_tuner *t, const char *path);
 int hc_tuner_load(hc_tuner *t, const char *path);
 void hc_tuner_free(hc_tuner *t);
 
+/* Checked builds only (libhc_checked.so, compiled with HC_CHECKED, the
+ * library's test variant): the number of device-side bounds violations
+ * counted since the last call -- staged-buffer and text reads of the scan
+ * kernels, spill-region and output accesses of the emit -- then reset.  A
+ * violating access is skipped or clamped, not made.  Synchronous.  Errors:
+ * HC_ERR_STATE in the regular build, HC_ERR_ARG, HC_ERR_CUDA. */
+int hc_check_bounds(uint64_t *violations);
+
 /* ------------------------------------------------------------------------
  * Served search: a request loop with continuous batching.
  *

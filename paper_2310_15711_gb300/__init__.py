@@ -97,6 +97,7 @@ SIGNATURES = {
     "hc_server_get_stats": (ctypes.c_int, [_vp, _vp]),
     "hc_server_destroy": (None, [_vp]),
     "hc_check_status": (ctypes.c_int, [_vp]),
+    "hc_check_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
     "hc_kernel_launches": (ctypes.c_uint64, []),
     "hc_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "hc_timing_report": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),

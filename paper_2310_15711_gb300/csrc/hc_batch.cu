@@ -645,6 +645,20 @@ int create_batch(const hc_batch_query* qs, size_t nq, const hc_tuner* tuner, hc_
 }
 
 }  // namespace
+int take_bound_violations_batch(uint64_t* count) {
+  *count = 0;
+#ifdef HC_CHECKED
+  unsigned long long v = 0, zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_bound_violations, sizeof v);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bound_violations, &zero, sizeof zero);
+  if (e != cudaSuccess) return cuda_error(e, "bound violation counter");
+  *count = v;
+  return HC_OK;
+#else
+  return HC_ERR_STATE;
+#endif
+}
+
 }  // namespace hc
 
 using namespace hc;

@@ -7,6 +7,22 @@
 
 namespace hc {
 
+// Checked builds (compiled with HC_CHECKED, the library's test variant):
+// HC_IN_BOUNDS(cond) tests an index condition and counts a failure in this
+// translation unit's violation counter (read by hc_check_bounds); callers
+// then skip or clamp the access instead of making it.  In the regular build
+// it is `true` and the condition is not evaluated.
+#ifdef HC_CHECKED
+static __device__ unsigned long long g_bound_violations;
+__device__ __forceinline__ bool checked_bound(bool ok) {
+  if (!ok) atomicAdd(&g_bound_violations, 1ull);
+  return ok;
+}
+#define HC_IN_BOUNDS(cond) (::hc::checked_bound(cond))
+#else
+#define HC_IN_BOUNDS(cond) (true)
+#endif
+
 // Upper bounds for every device-side wait.  A wait that exceeds them sets the
 // library's status flag and makes the kernel return instead of spinning on.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s of %globaltimer

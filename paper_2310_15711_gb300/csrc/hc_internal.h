@@ -96,6 +96,11 @@ cudaError_t launch_dependent(void (*fn)(KArgs...), unsigned grid, unsigned block
 TimingToken timing_begin(int kind, cudaStream_t stream);
 void timing_end(const TimingToken& t, cudaStream_t stream);
 
+// Checked builds: the bounds violations counted by the kernels of
+// hc_search.cu and hc_batch.cu since the last call (then reset).
+int take_bound_violations_search(uint64_t* count);
+int take_bound_violations_batch(uint64_t* count);
+
 // Copies the filter to the current device (once).  Returns an HC_* code.
 int filter_to_device(Filter* f);
 

@@ -125,9 +125,28 @@ __device__ __forceinline__ void load_qgram(const uint8_t* base, int o, uint32_t*
 
 template <int Q, bool STAGED>
 __device__ __forceinline__ uint32_t qgram_hash(const uint8_t* base, int o, const SearchArgs& a) {
+  // staged: the three words read from o's word lie in the staging buffer;
+  // unstaged: the q-gram lies in the text
+  if constexpr (STAGED) {
+    if (!HC_IN_BOUNDS(o >= 0 && o + 12 <= static_cast<int>(a.stage_bytes))) o = 0;
+  } else {
+    if (!HC_IN_BOUNDS(base + o >= a.y && base + o + Q <= a.y + a.n)) o = 0;
+  }
   uint32_t lo, hi;
   load_qgram<Q, STAGED>(base, o, &lo, &hi);
   return hash_bytes<Q>(lo, hi, a);
+}
+
+// Whether the m bytes of a window starting at chunk-relative `start` may be
+// read for verification (always true outside checked builds).
+template <bool STAGED>
+__device__ __forceinline__ bool window_in_bounds(const uint8_t* txt, int start, const SearchArgs& a,
+                                                 int head) {
+  if constexpr (STAGED) {
+    return HC_IN_BOUNDS(start >= -head && head + start + a.m <= static_cast<int>(a.stage_bytes));
+  } else {
+    return HC_IN_BOUNDS(txt + start >= a.y && txt + start + a.m <= a.y + a.n);
+  }
 }
 
 __device__ __forceinline__ bool verify_window(const uint8_t* w, const uint8_t* x, int m) {
@@ -210,8 +229,8 @@ __device__ __forceinline__ int warp_finish_window(const uint8_t* base, int head,
   if (vlast == a.hv) {
     const int start = ew - m + 1;
     const uint8_t* txt = base + head;
-    bool eq = true;
-    for (int k = lane; k < m; k += 32) eq &= text_byte<STAGED>(txt, start + k) == xv[k];
+    bool eq = window_in_bounds<STAGED>(txt, start, a, head);
+    for (int k = lane; eq && k < m; k += 32) eq &= text_byte<STAGED>(txt, start + k) == xv[k];
     *match = __all_sync(0xffffffffu, eq);
   }
   return ew + 1;
@@ -330,7 +349,7 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
       }
       // read in full (short window): H_v test, verification, advance by one
       const int start = e - m + 1;
-      bool eq = v == hv;
+      bool eq = v == hv && window_in_bounds<STAGED>(txt, start, a, head);
       for (int k = 0; eq && k < m; ++k) eq = text_byte<STAGED>(txt, start + k) == xv[k];
       if (eq) record_match<MODE>(sink, cnt++, start);
       e += 1;
@@ -473,7 +492,8 @@ __device__ __forceinline__ void warp_stream(const SearchArgs& a, unsigned long l
           const uint32_t rel = static_cast<uint32_t>(static_cast<unsigned long long>(i) * a.C);
           const unsigned long long ob = T + excl;
           if (cnt <= kSlots)
-            for (int k = 0; k < cnt; ++k) region[ob + k] = rel + sink.slot[k * kThreads];
+            for (int k = 0; k < cnt; ++k)
+              if (HC_IN_BOUNDS(ob + k < S)) region[ob + k] = rel + sink.slot[k * kThreads];
           // lanes with more than kSlots occurrences scan their segment again,
           // writing them all (the whole warp takes part)
           Sink w{};
@@ -584,7 +604,8 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
           while (s_U[rk + 1] <= u) ++rk;
           rec[uu] = rk;
           const uint2* r2 = reinterpret_cast<const uint2*>(a.region + (r0 + rk) * a.region_entries);
-          v[uu] = __ldcs(r2 + (u - s_U[rk]));
+          if (HC_IN_BOUNDS((u - s_U[rk]) * 2 + 2 <= a.region_entries)) v[uu] = __ldcs(r2 + (u - s_U[rk]));
+          else rec[uu] = -1;
         }
       }
 #pragma unroll
@@ -595,6 +616,7 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
         const unsigned long long e = (u - s_U[k]) * 2;   // first entry of the unit
         const unsigned long long vbase = (r0 + k) * a.chunks_per_cta * a.C;
         unsigned long long* o = a.pos + s_P[k] + e;
+        if (!HC_IN_BOUNDS(s_P[k] + e < a.cap && e < s_N[k])) continue;
         if (e + 2 <= s_N[k] && (reinterpret_cast<uintptr_t>(o) & 15u) == 0u) {
           *reinterpret_cast<ulonglong2*>(o) = make_ulonglong2(vbase + v[uu].x, vbase + v[uu].y);
         } else {

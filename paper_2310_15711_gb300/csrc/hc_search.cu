@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
       const int w0 = base + 16 * lane;      // first window of this lane
       uint32_t dg[4] = {~0u, ~0u, ~0u, ~0u};
       uint32_t cand = 0;
-      if (w0 < wins) {  // lanes past the chunk's end read nothing
+      // lanes past the chunk's end read nothing
+      if (w0 < wins && HC_IN_BOUNDS(a.head + w0 >= 0 && static_cast<uint32_t>(a.head + w0) + 24u <= a.stage_bytes)) {
         const uint32_t o = static_cast<uint32_t>(a.head + w0);
         const uint4 A = *reinterpret_cast<const uint4*>(sb + o);
         const uint2 B = *reinterpret_cast<const uint2*>(sb + o + 16);
@@ -636,6 +637,20 @@ int read_and_clear_status(cudaStream_t stream) {
   return HC_OK;
 }
 
+int take_bound_violations_search(uint64_t* count) {
+  *count = 0;
+#ifdef HC_CHECKED
+  unsigned long long v = 0, zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_bound_violations, sizeof v);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bound_violations, &zero, sizeof zero);
+  if (e != cudaSuccess) return cuda_error(e, "bound violation counter");
+  *count = v;
+  return HC_OK;
+#else
+  return HC_ERR_STATE;
+#endif
+}
+
 }  // namespace hc
 
 using namespace hc;
@@ -653,6 +668,19 @@ int check_search_args(const char* who, Filter* f, const uint8_t* y_dev, size_t n
 }  // namespace
 
 extern "C" {
+
+int hc_check_bounds(uint64_t* violations) {
+  clear_error();
+  if (violations == nullptr) return set_error(HC_ERR_ARG, "hc_check_bounds: violations is NULL");
+  *violations = 0;
+  uint64_t a = 0, b = 0;
+  int rc = take_bound_violations_search(&a);
+  if (rc == HC_ERR_STATE) return set_error(HC_ERR_STATE, "hc_check_bounds: not a checked build");
+  if (rc == HC_OK) rc = take_bound_violations_batch(&b);
+  if (rc != HC_OK) return rc;
+  *violations = a + b;
+  return HC_OK;
+}
 
 int hc_search_ex(const hc_filter* fp, const uint8_t* y_dev, size_t n, uint64_t* pos_dev,
                  size_t cap, uint64_t* count_dev, const hc_search_opts* opts,

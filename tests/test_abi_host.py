@@ -82,3 +82,11 @@ def test_null_filter_is_rejected():
     assert L.hc_filter_params(None, None, None, None, None) == hc.HC_ERR_ARG
     assert L.hc_search_async(None, None, 0, None, 0, None, None) == hc.HC_ERR_ARG
     L.hc_filter_free(None)  # no-op
+
+
+def test_check_bounds_refused_in_the_regular_build():
+    import ctypes
+    v = ctypes.c_uint64(7)
+    assert hc.lib().hc_check_bounds(ctypes.byref(v)) == hc.HC_ERR_STATE
+    assert v.value == 0
+    assert hc.lib().hc_check_bounds(None) == hc.HC_ERR_ARG
