@@ -27,6 +27,7 @@ no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import subprocess
@@ -360,6 +361,11 @@ def run_gpu(args, rank, world, local_rank):
 
     sampler = ClockSampler(local_rank)
     launches0 = hc.hc_kernel_launches()
+    # the host enqueues the searches; a garbage-collection pause long enough
+    # to drain the launch queue would leave the GPU idle inside the timed
+    # region, so the collector is off until the measurements are taken
+    gc.collect()
+    gc.disable()
     barrier()
     sampler.start()
     t_wall = time.perf_counter()
@@ -388,6 +394,7 @@ def run_gpu(args, rank, world, local_rank):
     hc.hc_timing_enable(False)
     kernel_times = hc.hc_timing_report(reset=True)   # {family: (ms, launches)}
     hc.hc_check_status(stream)
+    gc.enable()
     counts_tuned = counts.clone()
     paper = None
     if paper_cells is not None:
@@ -395,6 +402,8 @@ def run_gpu(args, rank, world, local_rank):
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
                 one_step(which=paper_cells)
+        gc.collect()
+        gc.disable()
         barrier()
         pe0, pe1 = ev(), ev()
         pe0.record(stream)
@@ -403,6 +412,7 @@ def run_gpu(args, rank, world, local_rank):
                 one_step(which=paper_cells)
         pe1.record(stream)
         barrier()
+        gc.enable()
         hc.hc_check_status(stream)
         p_s, p_bytes = combine_ranks(pe0.elapsed_time(pe1) / 1e3,
                                      sum(texts[s].numel() * args.patterns for (s, m) in keys) * args.steps,
