@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--tuner-table", default="",
                     help="load the autotuner's table from this file if it exists, else calibrate "
                          "and save it there (so that two runs use the same parameters)")
+    ap.add_argument("--clock-ms", type=int, default=200,
+                    help="nvidia-smi sampling interval during the timed region (0: no sampling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -108,17 +110,21 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 200, enabled: bool = True):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
+        self.enabled = enabled
         self.proc = None
         self.lines = []
         self._t = None
 
     def start(self):
+        if not self.enabled:
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -131,6 +137,8 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self):
+        if not self.enabled:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (--clock-ms 0)"]}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -359,7 +367,7 @@ def run_gpu(args, rank, world, local_rank):
     cell_ev = [[[ev(), ev()] for _ in range(ncell)] for _ in range(args.steps)]
     step_ev = [[ev(), ev()] for _ in range(args.steps)]
 
-    sampler = ClockSampler(local_rank)
+    sampler = ClockSampler(local_rank, interval_ms=max(args.clock_ms, 1), enabled=args.clock_ms > 0)
     launches0 = hc.hc_kernel_launches()
     # the host enqueues the searches; a garbage-collection pause long enough
     # to drain the launch queue would leave the GPU idle inside the timed
