@@ -66,6 +66,9 @@ def parse_args():
     ap.add_argument("--tuner-table", default="",
                     help="load the autotuner's table from this file if it exists, else calibrate "
                          "and save it there (so that two runs use the same parameters)")
+    ap.add_argument("--eager", action="store_true",
+                    help="enqueue every search from Python in the timed steps instead of replaying "
+                         "one CUDA graph per step")
     ap.add_argument("--clock-ms", type=int, default=200,
                     help="nvidia-smi sampling interval during the timed region (0: no sampling)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -99,6 +102,8 @@ def workload_config(args):
                     if getattr(args, "params", "paper") == "tuned" else
                     "paper's choice per text type and m (Tables 1-3), q clamped to m"),
         "l2": "inputs larger than L2 (256 MiB texts vs 129 MB L2); no flush",
+        "launch": ("eager enqueue of every search" if getattr(args, "eager", False)
+                   else "one CUDA graph per step (all its searches), replayed"),
     }
 
 
@@ -364,8 +369,26 @@ def run_gpu(args, rank, world, local_rank):
         raise RuntimeError("position buffer too small for this workload")
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    cell_ev = [[[ev(), ev()] for _ in range(ncell)] for _ in range(args.steps)]
     step_ev = [[ev(), ev()] for _ in range(args.steps)]
+    # the timed step is one CUDA graph of all its searches (captured once,
+    # replayed): the device runs them back to back whatever the host does
+    # meanwhile (an enqueue loop in Python can stall long enough to drain the
+    # launch queue); per-cell times come from events inside the graph
+    graph_cell_ev = [[ev(), ev()] for _ in range(ncell)]
+    graph = None
+    launches_per_step = None
+    if not args.eager:
+        graph = torch.cuda.CUDAGraph()
+        l0 = hc.hc_kernel_launches()
+        with torch.cuda.graph(graph, stream=stream):
+            one_step(graph_cell_ev)
+        launches_per_step = hc.hc_kernel_launches() - l0
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                graph.replay()
+        stream.synchronize()
+        hc.hc_check_status(stream)
+    cell_ev = [[[ev(), ev()] for _ in range(ncell)] for _ in range(args.steps)] if args.eager else None
 
     sampler = ClockSampler(local_rank, interval_ms=max(args.clock_ms, 1), enabled=args.clock_ms > 0)
     launches0 = hc.hc_kernel_launches()
@@ -381,13 +404,17 @@ def run_gpu(args, rank, world, local_rank):
     for k in range(args.steps):
         step_ev[k][0].record(stream)
         with torch.cuda.stream(stream):
-            one_step(cell_ev[k])
+            if graph is not None:
+                graph.replay()
+            else:
+                one_step(cell_ev[k])
         step_ev[k][1].record(stream)
     torch.cuda.nvtx.range_pop()
     barrier()
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
-    launches = hc.hc_kernel_launches() - launches0
+    launches = (hc.hc_kernel_launches() - launches0 if graph is None
+                else launches_per_step * args.steps)
     hc.hc_check_status(stream)
     # per-kernel durations: the same steps again with the library's event
     # timing on (an event between the scan and the emit kernel of a search
@@ -407,9 +434,14 @@ def run_gpu(args, rank, world, local_rank):
     paper = None
     if paper_cells is not None:
         # the same sweep on the paper's (q, alpha) (Tables 1-3), for comparison
+        pgraph = None
+        if not args.eager:
+            pgraph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(pgraph, stream=stream):
+                one_step(which=paper_cells)
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
-                one_step(which=paper_cells)
+                pgraph.replay() if pgraph is not None else one_step(which=paper_cells)
         gc.collect()
         gc.disable()
         barrier()
@@ -417,7 +449,7 @@ def run_gpu(args, rank, world, local_rank):
         pe0.record(stream)
         with torch.cuda.stream(stream):
             for _ in range(args.steps):
-                one_step(which=paper_cells)
+                pgraph.replay() if pgraph is not None else one_step(which=paper_cells)
         pe1.record(stream)
         barrier()
         gc.enable()
@@ -429,8 +461,12 @@ def run_gpu(args, rank, world, local_rank):
                  "counts_equal": bool(torch.equal(counts, counts_tuned))}
         counts.copy_(counts_tuned)
     step_ms = float(sum(e[0].elapsed_time(e[1]) for e in step_ev))
-    cell_ms = np.array([sum(cell_ev[k][ci][0].elapsed_time(cell_ev[k][ci][1])
-                            for k in range(args.steps)) for ci in range(ncell)])
+    if graph is not None:   # the last replay's cell times, for all steps
+        cell_ms = np.array([graph_cell_ev[ci][0].elapsed_time(graph_cell_ev[ci][1]) * args.steps
+                            for ci in range(ncell)])
+    else:
+        cell_ms = np.array([sum(cell_ev[k][ci][0].elapsed_time(cell_ev[k][ci][1])
+                                for k in range(args.steps)) for ci in range(ncell)])
 
     text_bytes_step = sum(texts[s].numel() * args.patterns for (s, m) in keys)
     step_s_max, job_bytes = combine_ranks(step_ms / 1e3, text_bytes_step * args.steps, dist, dev)
