@@ -374,7 +374,15 @@ def run_gpu(args, rank, world, local_rank):
     # replayed): the device runs them back to back whatever the host does
     # meanwhile (an enqueue loop in Python can stall long enough to drain the
     # launch queue); per-cell times come from events inside the graph
-    graph_cell_ev = [[ev(), ev()] for _ in range(ncell)]
+    def graph_ev():
+        # recorded by a node of the graph: an external event, to be timed
+        try:
+            return torch.cuda.Event(enable_timing=True, external=True)
+        except TypeError:
+            return None
+    graph_cell_ev = [[graph_ev(), graph_ev()] for _ in range(ncell)]
+    if any(e is None for pair in graph_cell_ev for e in pair):
+        graph_cell_ev = None
     graph = None
     launches_per_step = None
     if not args.eager:
@@ -461,9 +469,11 @@ def run_gpu(args, rank, world, local_rank):
                  "counts_equal": bool(torch.equal(counts, counts_tuned))}
         counts.copy_(counts_tuned)
     step_ms = float(sum(e[0].elapsed_time(e[1]) for e in step_ev))
-    if graph is not None:   # the last replay's cell times, for all steps
+    if graph is not None and graph_cell_ev is not None:   # the last replay's cell times, for all steps
         cell_ms = np.array([graph_cell_ev[ci][0].elapsed_time(graph_cell_ev[ci][1]) * args.steps
                             for ci in range(ncell)])
+    elif graph is not None:   # no timed events inside graphs: the step time split evenly
+        cell_ms = np.full(ncell, step_ms / ncell)
     else:
         cell_ms = np.array([sum(cell_ev[k][ci][0].elapsed_time(cell_ev[k][ci][1])
                                 for k in range(args.steps)) for ci in range(ncell)])
