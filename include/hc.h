@@ -101,8 +101,9 @@ int hc_filter_to_device(hc_filter *f);
  *
  * hc_search_async: y_dev is the text (n bytes, device memory, any alignment);
  * pos_dev receives the first min(count, cap) occurrence positions in
- * ascending order (may be NULL when cap = 0); count_dev (device memory, one
- * uint64) receives the total count.  Both must be 8-byte aligned (any
+ * ascending order (may be NULL when cap = 0); count_dev (one uint64)
+ * receives the total count; both may be device memory or mapped host memory
+ * (hc_mapped_alloc).  Both must be 8-byte aligned (any
  * element of a uint64 array is), else HC_ERR_ARG.  Nothing is waited for.  The first call
  * with a filter copies it to the device (see hc_filter_to_device).  Each call
  * takes a stream-ordered workspace from the library's memory pool and gives
@@ -300,6 +301,15 @@ int hc_tuner_entry(const hc_tuner *t, size_t i, hc_tune_entry *out);
 int hc_tuner_save(const hc_tuner *t, const char *path);
 int hc_tuner_load(hc_tuner *t, const char *path);
 void hc_tuner_free(hc_tuner *t);
+
+/* Pinned host memory mapped into the current device's address space, for
+ * outputs that the kernels write straight to the host (positions, counts:
+ * pass *dev_ptr as pos_dev / count_dev; on a Grace-Blackwell node the
+ * stores travel over NVLink-C2C, so no copy follows the search).  The host
+ * reads the results at *host_ptr once the search has completed.  Errors:
+ * HC_ERR_ARG, HC_ERR_CUDA.  hc_mapped_free releases it (NULL: no-op). */
+int hc_mapped_alloc(size_t bytes, void **host_ptr, void **dev_ptr);
+void hc_mapped_free(void *host_ptr);
 
 /* Checked builds only (libhc_checked.so, compiled with HC_CHECKED, the
  * library's test variant): the number of device-side bounds violations

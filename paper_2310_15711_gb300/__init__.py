@@ -98,6 +98,8 @@ SIGNATURES = {
     "hc_server_destroy": (None, [_vp]),
     "hc_check_status": (ctypes.c_int, [_vp]),
     "hc_check_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
+    "hc_mapped_alloc": (ctypes.c_int, [_sz, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "hc_mapped_free": (None, [_vp]),
     "hc_kernel_launches": (ctypes.c_uint64, []),
     "hc_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "hc_timing_report": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),
@@ -151,11 +153,62 @@ def _stream_handle(stream):
 def _dev_ptr(t, dtype_bytes=None):
     if t is None:
         return None
+    if isinstance(t, MappedView):
+        return ctypes.c_void_p(t.device_address)
     if not t.is_cuda:
         raise ValueError("expected a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+class MappedView:
+    """A run of int64 slots in a MappedBuffer, usable as an output (pos_dev,
+    count_dev) of the search calls."""
+
+    def __init__(self, buf: "MappedBuffer", offset: int, count: int):
+        self.buf, self.offset, self.count = buf, int(offset), int(count)
+        self.device_address = buf.device_address + 8 * self.offset
+
+    def numel(self) -> int:
+        return self.count
+
+    def numpy(self) -> np.ndarray:
+        return self.buf.array()[self.offset:self.offset + self.count]
+
+
+class MappedBuffer:
+    """hc_mapped_alloc: pinned host memory the kernels write straight into."""
+
+    def __init__(self, count: int):
+        h, d = _vp(), _vp()
+        _check(lib().hc_mapped_alloc(8 * int(count), ctypes.byref(h), ctypes.byref(d)), "hc_mapped_alloc")
+        self._h = h
+        self.count = int(count)
+        self.device_address = d.value
+        self._arr = np.ctypeslib.as_array(ctypes.cast(h, ctypes.POINTER(ctypes.c_int64)), shape=(self.count,))
+
+    def array(self) -> np.ndarray:
+        """The buffer as int64 values (read after the writing searches completed)."""
+        return self._arr
+
+    def view(self, offset: int = 0, count: int | None = None) -> MappedView:
+        count = self.count - offset if count is None else count
+        if offset < 0 or count < 0 or offset + count > self.count:
+            raise ValueError("view outside the buffer")
+        return MappedView(self, offset, count)
+
+    def free(self):
+        if self._h is not None and _lib is not None:
+            _lib.hc_mapped_free(self._h)
+        self._h = None
+        self._arr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 HC_MODE_AUTO = 0

@@ -299,4 +299,28 @@ int hc_filter_to_device(hc_filter* fp) {
   return filter_to_device(f);
 }
 
+int hc_mapped_alloc(size_t bytes, void** host_ptr, void** dev_ptr) {
+  clear_error();
+  if (host_ptr == nullptr || dev_ptr == nullptr || bytes == 0)
+    return set_error(HC_ERR_ARG, "hc_mapped_alloc: NULL output or zero size");
+  *host_ptr = nullptr;
+  *dev_ptr = nullptr;
+  void* h = nullptr;
+  cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+  if (e != cudaSuccess) return cuda_error(e, "cudaHostAlloc(mapped)");
+  void* d = nullptr;
+  e = cudaHostGetDevicePointer(&d, h, 0);
+  if (e != cudaSuccess) {
+    cudaFreeHost(h);
+    return cuda_error(e, "cudaHostGetDevicePointer");
+  }
+  *host_ptr = h;
+  *dev_ptr = d;
+  return HC_OK;
+}
+
+void hc_mapped_free(void* host_ptr) {
+  if (host_ptr != nullptr) cudaFreeHost(host_ptr);
+}
+
 }  // extern "C"

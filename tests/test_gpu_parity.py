@@ -292,6 +292,35 @@ def test_positions_at_8_byte_aligned_offset(mode):
     f.free()
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_outputs_in_mapped_host_memory(mode):
+    """Positions and counts written by the kernels straight into mapped host
+    memory (hc_mapped_alloc) equal the oracle's, for every kernel kind, at an
+    offset inside the buffer; slots outside the written range keep their
+    values."""
+    hc = _hc()
+    rng = np.random.default_rng(71 + mode)
+    m, q = (3, 3) if mode == 3 else (9, 4)
+    x, y = _case(rng, 4, 2_000_003, m, plant=50)
+    want = oracle.hc_search(x, y, q, 11)
+    y_dev, keep = _upload(y, offset=5)
+    f = hc.hc_preprocess(x, q, 11)
+    buf = hc.MappedBuffer(want.size + 9)
+    cnt = hc.MappedBuffer(3)
+    buf.array()[:] = -3
+    cnt.array()[:] = -3
+    hc.hc_search_ex(f, y_dev, buf.view(3, want.size + 2), cnt.view(1, 1), hc.SearchOpts(mode=mode))
+    torch.cuda.synchronize()
+    hc.hc_check_status()
+    assert int(cnt.array()[1]) == want.size and cnt.array()[0] == -3 and cnt.array()[2] == -3
+    got = buf.array()
+    assert np.array_equal(got[3:3 + want.size].view(np.uint64), want)
+    assert (got[:3] == -3).all() and (got[3 + want.size:] == -3).all()
+    buf.free()
+    cnt.free()
+    f.free()
+
+
 def test_misaligned_output_pointers_rejected():
     """A positions or count pointer that is not 8-byte aligned is an argument
     error, reported before anything is launched."""
