@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--tuner-table", default="",
                     help="load the autotuner's table from this file if it exists, else calibrate "
                          "and save it there (so that two runs use the same parameters)")
+    ap.add_argument("--pos64", action="store_true",
+                    help="positions as uint64 instead of uint32 (the sweep's texts are < 2^32 bytes)")
     ap.add_argument("--eager", action="store_true",
                     help="enqueue every search from Python in the timed steps instead of replaying "
                          "one CUDA graph per step")
@@ -104,6 +106,7 @@ def workload_config(args):
         "l2": "inputs larger than L2 (256 MiB texts vs 129 MB L2); no flush",
         "launch": ("eager enqueue of every search" if getattr(args, "eager", False)
                    else "one CUDA graph per step (all its searches), replayed"),
+        "positions": "uint64" if getattr(args, "pos64", False) else "uint32 (texts < 2^32 bytes)",
     }
 
 
@@ -310,6 +313,10 @@ def run_gpu(args, rank, world, local_rank):
                 tuner.save(args.tuner_table)
         tune_s = time.perf_counter() - t0
 
+    # positions as uint32 (the texts are far below 2^32 bytes) unless --pos64
+    pos32 = 0 if args.pos64 else 1
+    pos_bytes = 8 if args.pos64 else 4
+
     # ---- inputs
     texts_np = {s: hi.sweep_text(s, args.n) for s in sigmas}
     texts = {s: torch.from_numpy(t).to(dev) for s, t in texts_np.items()}
@@ -318,13 +325,13 @@ def run_gpu(args, rank, world, local_rank):
         out = {}
         for s, m in grid:
             pats = hi.sweep_patterns(texts_np[s], s, m, args.patterns)
-            opts = None
             if kind == "tuned":
                 e = tuner.lookup(s, m)
                 q, alpha = e["q"], e["alpha"]
-                opts = hc.SearchOpts(lane_bytes=e["lane_bytes"], mode=e["mode"])
+                opts = hc.SearchOpts(lane_bytes=e["lane_bytes"], mode=e["mode"], pos32=pos32)
             else:
                 q, alpha = hi.paper_q_alpha(s, m)
+                opts = hc.SearchOpts(pos32=pos32)
             filters = []
             for x in pats:
                 f = hc.hc_preprocess(x, q, alpha)
@@ -336,7 +343,7 @@ def run_gpu(args, rank, world, local_rank):
     cells = make_cells(args.params)
     paper_cells = make_cells("paper") if args.params == "tuned" else None
     cap = 1 << 27
-    pos = torch.empty(cap, dtype=torch.int64, device=dev)
+    pos = torch.empty(cap, dtype=torch.int64 if args.pos64 else torch.int32, device=dev)
     ncell = len(cells)
     counts = torch.zeros((ncell, args.patterns), dtype=torch.int64, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -485,7 +492,7 @@ def run_gpu(args, rank, world, local_rank):
 
     # algorithmic bytes per kernel family (per step): the scan kernels read
     # the text once and spill 4 bytes per occurrence; the emit kernel reads
-    # those 4 and writes the 8-byte position
+    # those 4 and writes the position (4 or 8 bytes)
     cnt = counts.cpu().numpy()
     fam_bytes = {}
     per_cell = {}
@@ -495,12 +502,12 @@ def run_gpu(args, rank, world, local_rank):
         occ = float(cnt[ci].sum())
         fam = scan_family(m, q, opts.mode if opts is not None else 0)
         fam_bytes[fam] = fam_bytes.get(fam, 0.0) + n * args.patterns + 4 * occ
-        fam_bytes["emit"] = fam_bytes.get("emit", 0.0) + 12 * occ
+        fam_bytes["emit"] = fam_bytes.get("emit", 0.0) + (4 + pos_bytes) * occ
         cell_s = cell_ms[ci] / 1e3
         # algorithmic DRAM bytes of the cell's searches: the text (every byte
         # is read when the whole text is staged; direct-mode cells read less),
-        # 4 per spilled occurrence, 12 per emitted one (read 4, write 8)
-        alg = (n * args.patterns + 16 * occ) * args.steps
+        # 4 per spilled occurrence, 4 + the position's bytes per emitted one
+        alg = (n * args.patterns + (8 + pos_bytes) * occ) * args.steps
         per_cell[f"s{s}_m{m}"] = {
             "GBps": round(n * args.patterns * args.steps / cell_s / GB, 1),
             "kernel": fam, "q": q, "alpha": alpha,
@@ -542,7 +549,7 @@ def run_gpu(args, rank, world, local_rank):
         fr = sorted(f for _, f in small)
         line["m_le_32"] = {"cells": len(fr), "at_or_above_0.60": sum(1 for f in fr if f >= 0.60),
                            "median_hbm_frac": fr[len(fr) // 2], "min": fr[0], "max": fr[-1],
-                           "note": "per cell: algorithmic bytes of its searches (text + 16 per "
+                           "note": f"per cell: algorithmic bytes of its searches (text + {8 + pos_bytes} per "
                                    "occurrence) / its device time, of measured HBM"}
     if paper is not None:
         line["paper_params"] = paper
@@ -551,7 +558,7 @@ def run_gpu(args, rank, world, local_rank):
     # ---- end to end through the synchronous C-ABI call, host buffers
     if not args.no_e2e:
         line["e2e"] = e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream, dist,
-                               expect=counts_tuned.cpu().numpy())
+                               expect=counts_tuned.cpu().numpy(), pos_bytes=pos_bytes)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(texts_np, {k: v[0] for k, v in cells.items()},
                                             args.cpu_seconds, os.cpu_count() or 1)
@@ -853,7 +860,7 @@ def combine_ranks(seconds, units, dist=None, device=None):
     return float(t.item()), float(u.item())
 
 
-def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream, dist=None, expect=None):
+def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream, dist=None, expect=None, pos_bytes=8):
     """One sweep step end to end through the C ABI with host buffers: per
     sigma the text is copied from pinned host memory to the device, then every
     pattern of every cell is searched (hc_search_ex, stream-ordered) and each
@@ -864,9 +871,9 @@ def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream, dist=None, exp
     synchronised and the counts read on the host."""
     pinned = {s: torch.from_numpy(t).pin_memory() for s, t in texts_np.items()}
     y_dev = torch.empty(max(t.numel() for t in pinned.values()), dtype=torch.uint8, device=dev)
-    cap = 1 << 27
+    cap = 1 << 27                    # positions (of pos_bytes each)
     nsearch = sum(len(cells[k][1]) for k in keys)
-    host_pos = hc.MappedBuffer(cap)
+    host_pos = hc.MappedBuffer(cap * pos_bytes // 8)
     host_cnt = hc.MappedBuffer(nsearch)
     h2d = 0
     text_bytes = 0
@@ -885,7 +892,7 @@ def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream, dist=None, exp
                     continue
                 pats, filters, q, alpha, opts = cells[key]
                 for f in filters:
-                    hc.hc_search_ex(f, y_dev[:n], host_pos.view(0, cap), host_cnt.view(i, 1), opts,
+                    hc.hc_search_ex(f, y_dev[:n], host_pos.view(), host_cnt.view(i, 1), opts,
                                     cap=cap, stream=stream)
                     i += 1
                     text_bytes += n
@@ -893,7 +900,7 @@ def e2e_step(args, hc, torch, dev, texts_np, cells, keys, stream, dist=None, exp
     counts = host_cnt.array().copy()
     dt = time.perf_counter() - t0
     hc.hc_check_status(stream)
-    d2h = int(sum(8 * min(int(c), cap) + 8 for c in counts))
+    d2h = int(sum(pos_bytes * min(int(c), cap) + 8 for c in counts))
     same = None if expect is None else bool(np.array_equal(counts, expect.reshape(-1)))
     host_pos.free()
     host_cnt.free()

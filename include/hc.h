@@ -150,7 +150,9 @@ typedef struct hc_search_opts {
     int mode;
     uint64_t spill_entries;
     int speculate;
-    int reserved;
+    int pos32;              /* 1: positions written as uint32 (pos_dev holds cap
+                               uint32 values, 4-byte aligned; needs
+                               n - m + 1 <= 2^32); 0: uint64 */
 } hc_search_opts;
 
 /* hc_search_ex: hc_search_async with explicit launch options (opts may be

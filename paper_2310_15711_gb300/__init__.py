@@ -225,12 +225,12 @@ class SearchOpts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("lane_bytes", ctypes.c_int),
                 ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("mode", ctypes.c_int), ("spill_entries", ctypes.c_uint64),
-                ("speculate", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("speculate", ctypes.c_int), ("pos32", ctypes.c_int)]
 
     def __init__(self, lane_bytes=0, stages=0, ctas_per_sm=0, spill_entries=0, mode=0,
-                 speculate=0):
+                 speculate=0, pos32=0):
         super().__init__(ctypes.sizeof(SearchOpts), int(lane_bytes), int(stages),
-                         int(ctas_per_sm), int(mode), int(spill_entries), int(speculate), 0)
+                         int(ctas_per_sm), int(mode), int(spill_entries), int(speculate), int(pos32))
 
 
 class HCFilter:

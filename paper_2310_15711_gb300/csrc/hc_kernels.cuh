@@ -45,6 +45,7 @@ struct SearchArgs {
   uint32_t mask, hv;
   unsigned long long* pos;   // output positions (device), cap of them
   unsigned long long cap;
+  int pos32;                 // 1: positions are uint32 values at pos (cap of them)
   unsigned long long* count_out;
   // workspace (no zeroing needed: the scan kernel writes every entry it or
   // the emit kernel reads)
@@ -163,6 +164,7 @@ struct Sink {
   uint32_t* region;          // kToRegion: region[obase + i] = vbase + start
   unsigned long long* pos;   // kToPositions: pos[obase + i] = vbase + start
   unsigned long long obase, vbase, limit;
+  int pos32;                 // kToPositions: pos holds uint32 values
 };
 
 // Records one occurrence (window start `start`, chunk-relative) as the
@@ -176,6 +178,8 @@ __device__ __forceinline__ void record_match(const Sink& sink, int cnt, int star
     if (idx < sink.limit) {
       if constexpr (MODE == kToRegion)
         sink.region[idx] = static_cast<uint32_t>(sink.vbase + static_cast<unsigned>(start));
+      else if (sink.pos32)
+        reinterpret_cast<uint32_t*>(sink.pos)[idx] = static_cast<uint32_t>(sink.vbase + static_cast<unsigned>(start));
       else
         sink.pos[idx] = sink.vbase + static_cast<unsigned long long>(start);
     }
@@ -615,8 +619,19 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
         const unsigned long long u = u0 + static_cast<unsigned long long>(uu) * stride;
         const unsigned long long e = (u - s_U[k]) * 2;   // first entry of the unit
         const unsigned long long vbase = (r0 + k) * a.chunks_per_cta * a.C;
-        unsigned long long* o = a.pos + s_P[k] + e;
         if (!HC_IN_BOUNDS(s_P[k] + e < a.cap && e < s_N[k])) continue;
+        if (a.pos32) {
+          uint32_t* o = reinterpret_cast<uint32_t*>(a.pos) + s_P[k] + e;
+          const uint32_t b32 = static_cast<uint32_t>(vbase);
+          if (e + 2 <= s_N[k] && (reinterpret_cast<uintptr_t>(o) & 7u) == 0u) {
+            *reinterpret_cast<uint2*>(o) = make_uint2(b32 + v[uu].x, b32 + v[uu].y);
+          } else {
+            o[0] = b32 + v[uu].x;
+            if (e + 1 < s_N[k]) o[1] = b32 + v[uu].y;
+          }
+          continue;
+        }
+        unsigned long long* o = a.pos + s_P[k] + e;
         if (e + 2 <= s_N[k] && (reinterpret_cast<uintptr_t>(o) & 15u) == 0u) {
           *reinterpret_cast<ulonglong2*>(o) = make_ulonglong2(vbase + v[uu].x, vbase + v[uu].y);
         } else {
@@ -670,6 +685,7 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
           if (mine) {  // warp-uniform: scan_segment is called by whole warps
             Sink w{};
             w.pos = a.pos;
+            w.pos32 = a.pos32;
             w.obase = out + excl;
             w.vbase = cs;
             w.limit = a.cap;

@@ -445,6 +445,7 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   // per-lane form on every sweep cell (each first-test hit serialises the
   // warp), so the automatic choice is the per-lane form
   if (kind != HC_MODE_DENSE) p.spec = o != nullptr && o->speculate > 0;
+  p.pos32 = o != nullptr && o->pos32 == 1;
 
   int rc = ensure_smem_attr(dev, p.scan, p.smem_scan);
   if (rc != HC_OK) return rc;
@@ -536,6 +537,7 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   a.stages = p.stages;
   a.records = p.records;
   a.spec = p.spec ? 1 : 0;
+  a.pos32 = p.pos32 ? 1 : 0;
   a.emit_group = p.emit_group;
   // byte groups of h: the longest prefix whose weights 2^(s*k) fit in a byte
   const int s = f->s, q = f->q;
@@ -657,12 +659,15 @@ using namespace hc;
 
 namespace {
 int check_search_args(const char* who, Filter* f, const uint8_t* y_dev, size_t n,
-                      const uint64_t* pos_dev, size_t cap) {
+                      const uint64_t* pos_dev, size_t cap, bool pos32 = false) {
   if (f == nullptr) return set_error(HC_ERR_ARG, std::string(who) + ": invalid filter");
   if (y_dev == nullptr && n > 0) return set_error(HC_ERR_ARG, std::string(who) + ": y_dev is NULL");
   if (pos_dev == nullptr && cap > 0)
     return set_error(HC_ERR_ARG, std::string(who) + ": pos_dev is NULL with cap > 0");
-  if (!aligned8(pos_dev)) return set_error(HC_ERR_ARG, std::string(who) + ": pos_dev not 8-byte aligned");
+  if (pos32 ? (reinterpret_cast<uintptr_t>(pos_dev) & 3u) != 0 : !aligned8(pos_dev))
+    return set_error(HC_ERR_ARG, std::string(who) + (pos32 ? ": pos_dev not 4-byte aligned" : ": pos_dev not 8-byte aligned"));
+  if (pos32 && n >= f->m && n - f->m + 1 > (uint64_t(1) << 32))
+    return set_error(HC_ERR_ARG, std::string(who) + ": uint32 positions need n - m + 1 <= 2^32");
   return HC_OK;
 }
 }  // namespace
@@ -687,12 +692,14 @@ int hc_search_ex(const hc_filter* fp, const uint8_t* y_dev, size_t n, uint64_t* 
                  hc_stream_t stream) {
   clear_error();
   Filter* f = as_filter(fp);
-  int rc = check_search_args("hc_search_ex", f, y_dev, n, pos_dev, cap);
+  if (opts != nullptr && opts->struct_size != sizeof(hc_search_opts))
+    return set_error(HC_ERR_ARG, "hc_search_ex: opts->struct_size mismatch");
+  if (opts != nullptr && opts->pos32 != 0 && opts->pos32 != 1)
+    return set_error(HC_ERR_ARG, "hc_search_ex: pos32 must be 0 or 1");
+  int rc = check_search_args("hc_search_ex", f, y_dev, n, pos_dev, cap, opts != nullptr && opts->pos32 == 1);
   if (rc != HC_OK) return rc;
   if (count_dev == nullptr || !aligned8(count_dev))
     return set_error(HC_ERR_ARG, "hc_search_ex: count_dev is NULL or not 8-byte aligned");
-  if (opts != nullptr && opts->struct_size != sizeof(hc_search_opts))
-    return set_error(HC_ERR_ARG, "hc_search_ex: opts->struct_size mismatch");
   return launch_search(f, y_dev, n, pos_dev, cap, count_dev, opts,
                        reinterpret_cast<cudaStream_t>(stream));
 }

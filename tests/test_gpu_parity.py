@@ -321,6 +321,55 @@ def test_outputs_in_mapped_host_memory(mode):
     f.free()
 
 
+@pytest.mark.parametrize("opts", [dict(pos32=1), dict(pos32=1, mode=1), dict(pos32=1, mode=2),
+                                  dict(pos32=1, spill_entries=1), dict(pos32=1, mode=2, spill_entries=3)])
+def test_uint32_positions(opts):
+    """pos32: the same positions as uint32 values, at a 4-byte (not 8-byte)
+    aligned output, through every kernel kind, re-scans of overflowed spill
+    regions and capacity truncation; nothing outside the output is written."""
+    hc = _hc()
+    rng = np.random.default_rng(81)
+    for sigma, m, q, n in [(2, 3, 3, 700_001), (4, 8, 4, 1_500_000), (20, 2, 2, 333_333), (4, 4, 4, 600_000)]:
+        if opts.get("mode") in (1, 2) and m == q and m < 3:
+            continue
+        x, y = _case(rng, sigma, n, m, plant=50)
+        want = oracle.hc_search(x, y, q, 11)
+        y_dev, keep = _upload(y, offset=int(rng.integers(0, 16)))
+        f = hc.hc_preprocess(x, q, 11)
+        for cap in (want.size + 3, max(want.size // 3, 1)):
+            buf = torch.full((cap + 6,), -7, dtype=torch.int32, device="cuda")
+            pos = buf[1:1 + cap]
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(**opts))
+            torch.cuda.synchronize()
+            hc.hc_check_status()
+            assert int(cnt.item()) == want.size, (sigma, m, opts)
+            k = min(cap, want.size)
+            got = buf.cpu().numpy()
+            assert np.array_equal(got[1:1 + k].view(np.uint32).astype(np.uint64), want[:k]), (sigma, m, opts, cap)
+            assert got[0] == -7 and (got[1 + k:] == -7).all()
+        f.free()
+
+
+def test_uint32_positions_rejected_when_misaligned_or_invalid():
+    hc = _hc()
+    y_dev, keep = _upload(np.frombuffer(b"ACGT" * 1000, np.uint8))
+    f = hc.hc_preprocess(b"ACGTACGT", 4, 12)
+    raw = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(hc.HCError) as ei:                      # 2-byte aligned
+        hc.hc_search_ex(f, y_dev, raw[2:66], cnt, hc.SearchOpts(pos32=1), cap=16)
+    assert ei.value.code == hc.HC_ERR_ARG
+    with pytest.raises(hc.HCError) as ei:
+        hc.hc_search_ex(f, y_dev, raw[4:68], cnt, hc.SearchOpts(pos32=2), cap=16)
+    assert ei.value.code == hc.HC_ERR_ARG
+    hc.hc_search_ex(f, y_dev, raw[4:68], cnt, hc.SearchOpts(pos32=1), cap=16)   # 4-byte aligned: fine
+    torch.cuda.synchronize()
+    hc.hc_check_status()
+    assert int(cnt.item()) == 999
+    f.free()
+
+
 def test_misaligned_output_pointers_rejected():
     """A positions or count pointer that is not 8-byte aligned is an argument
     error, reported before anything is launched."""
