@@ -20,6 +20,12 @@ host cores, and SM clocks sampled during the timed region.
 ``--impl reference`` times the CPU oracle (the plain C HC of the paper's
 Fig. 4/5) instead, on a bounded sample of the same workload.
 
+``--workload skewed`` runs the same measurement on the skewed config: one
+1 GiB text from an order-2 Markov source over 60 symbols (Zipf(1.1)
+unigrams), m in {4, 8, ..., 1024}, P patterns per m copied from the text.
+``--workload batched`` and ``--workload served`` are described at their
+functions.
+
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
 torchrun, one process per GPU, each searching the full sweep (weak scaling,
 no collective on the data path).
@@ -46,6 +52,8 @@ import hc_inputs as hi  # noqa: E402
 GB = 1e9
 SERVED_RATES_DEFAULT = (1000, 10000, 50000)
 METRIC = "text GB/s searched (device-timed), plain HC sweep"
+SKEW_METRIC = "text GB/s searched (device-timed), skewed Markov text"
+SKEW_KEY = 60        # the skewed text's alphabet size, its key among the texts
 UNIT = "GB/s"
 
 
@@ -76,10 +84,12 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["sweep", "batched", "served"], default="sweep",
-                    help="sweep: the plain-HC sweep (default); batched: 4096 queries in one "
-                         "graph-captured batch vs. one plain launch per query; served: Poisson "
-                         "request streams into the server vs. a plain per-request server")
+    ap.add_argument("--workload", choices=["sweep", "skewed", "batched", "served"], default="sweep",
+                    help="sweep: the plain-HC sweep (default); skewed: the 1 GiB order-2 Markov "
+                         "text; batched: 4096 queries in one graph-captured batch vs. one plain "
+                         "launch per query; served: Poisson request streams into the server vs. "
+                         "a plain per-request server")
+    ap.add_argument("--skew-n", type=int, default=1 << 30, help="skewed text length")
     ap.add_argument("--served-rates", type=int, nargs="+", default=list(SERVED_RATES_DEFAULT))
     ap.add_argument("--served-seconds", type=float, default=2.0)
     ap.add_argument("--served-backlog", type=int, default=50000,
@@ -90,7 +100,56 @@ def parse_args():
     return ap.parse_args()
 
 
+def metric_for(args):
+    return SKEW_METRIC if getattr(args, "workload", "sweep") == "skewed" else METRIC
+
+
+def skew_sigma_eff(y: np.ndarray) -> float:
+    """Effective alphabet size of a text, 1 / sum of squared symbol
+    frequencies (the alphabet size of a uniform text with the same chance
+    that two random positions hold the same symbol), from its first 64 MiB."""
+    c = np.bincount(y[:1 << 26], minlength=256).astype(np.float64)
+    p = c / c.sum()
+    return float(1.0 / np.sum(p * p))
+
+
+def workload_inputs(args, patterns: int):
+    """Texts (host arrays keyed by an alphabet size), the (key, m) cells, and
+    per cell the patterns, of the sweep or the skewed workload."""
+    if getattr(args, "workload", "sweep") == "skewed":
+        texts = {SKEW_KEY: hi.skew_text(args.skew_n)}
+        grid = [(SKEW_KEY, m) for m in hi.SKEW_MS]
+    else:
+        grid = [(s, m) for s in hi.SWEEP_SIGMAS for m in hi.SWEEP_MS]
+        texts = None
+    if args.cells:
+        grid = [tuple(int(v) for v in c.split(":")) for c in args.cells.split(",")]
+    if texts is None:
+        texts = {s: hi.sweep_text(s, args.n) for s in sorted({s for s, _ in grid})}
+    pats = {(s, m): hi.sweep_patterns(texts[s], s, m, patterns) for s, m in grid}
+    return texts, grid, pats
+
+
 def workload_config(args):
+    if getattr(args, "workload", "sweep") == "skewed":
+        return {
+            "workload": "plain HC, skewed text",
+            "text_bytes": args.skew_n,
+            "text": "order-2 Markov source over 60 symbols (bytes 65..124), Zipf(1.1) unigrams, "
+                    "seeded transition rows; patterns copied from the text",
+            "cells": args.cells or "all",
+            "ms": list(hi.SKEW_MS),
+            "patterns_per_cell": args.patterns,
+            "q_alpha": ("autotuned on uniform calibration texts over the text's effective alphabet "
+                        "size (1 / sum of squared symbol frequencies); paper_params gives the "
+                        "paper's English column (nearest alphabet size)"
+                        if getattr(args, "params", "paper") == "tuned" else
+                        "paper's English column (Tables 1-3), the nearest alphabet size"),
+            "l2": f"inputs larger than L2 ({args.skew_n >> 20} MiB text vs 129 MB L2); no flush",
+            "launch": ("eager enqueue of every search" if getattr(args, "eager", False)
+                       else "one CUDA graph per step (all its searches), replayed"),
+            "positions": "uint64" if getattr(args, "pos64", False) else "uint32 (texts < 2^32 bytes)",
+        }
     return {
         "workload": "plain HC sweep",
         "text_bytes_per_sigma": args.n,
@@ -229,6 +288,7 @@ def cpu_baseline(texts, cells, seconds: float, threads: int):
     import oracle
     oracle.build()
     prefix = 1 << 24
+    full = max(t.size for t in texts.values())
     total_bytes, total_t, searched = 0, 0.0, 0
     k = 0
     t_start = time.perf_counter()
@@ -246,7 +306,7 @@ def cpu_baseline(texts, cells, seconds: float, threads: int):
     return {"value": total_bytes / total_t / GB, "unit": UNIT, "cores": threads,
             "kind": "oracle",
             "sample": f"{searched} searches: {len(cells)} cells x {k} pattern(s) each, "
-                      f"first {prefix >> 20} MiB of each 256 MiB text, "
+                      f"first {prefix >> 20} MiB of each {full >> 20} MiB text, "
                       f"{threads} threads over pieces overlapping by m-1"}
 
 
@@ -254,9 +314,7 @@ def run_reference(args, rank, world):
     """--impl reference: the CPU oracle as the reference arm."""
     if rank != 0:
         return
-    texts = {s: hi.sweep_text(s, args.n) for s in hi.SWEEP_SIGMAS}
-    cells = {(s, m): hi.sweep_patterns(texts[s], s, m, max(1, min(args.patterns, 4)))
-             for s in hi.SWEEP_SIGMAS for m in hi.SWEEP_MS}
+    texts, _, cells = workload_inputs(args, max(1, min(args.patterns, 4)))
     threads = os.cpu_count() or 1
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
@@ -268,7 +326,7 @@ def run_reference(args, rank, world):
     wall = time.perf_counter() - t0
     v = float(np.mean([c["value"] for c in vals]))
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": metric_for(args), "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic", "config": workload_config(args),
@@ -294,10 +352,12 @@ def run_gpu(args, rank, world, local_rank):
 
     # ---- parameters: measured per (sigma, m) on this GPU by the autotuner
     # (single-search path, its own calibration texts), unless --params paper
-    grid = [(s, m) for s in hi.SWEEP_SIGMAS for m in hi.SWEEP_MS]
-    if args.cells:
-        grid = [tuple(int(v) for v in c.split(":")) for c in args.cells.split(",")]
+    texts_np, grid, patterns = workload_inputs(args, args.patterns)
     sigmas = sorted({s for s, _ in grid})
+    # the alphabet size the tuner's table is read at: a uniform text's own,
+    # the skewed text's effective one
+    tune_sigma = {s: (max(2, int(round(skew_sigma_eff(texts_np[s])))) if args.workload == "skewed" else s)
+                  for s in sigmas}
     tune_s = None
     tuner = None
     if args.params == "tuned":
@@ -306,8 +366,8 @@ def run_gpu(args, rank, world, local_rank):
         if args.tuner_table and os.path.exists(args.tuner_table):
             tuner.load(args.tuner_table)
         else:
-            tuner.calibrate(sigmas, sorted({m for _, m in grid}), text_bytes=args.n, seed=21,
-                            path=hc.HC_TUNE_SINGLE)
+            tuner.calibrate(sorted(set(tune_sigma.values())), sorted({m for _, m in grid}),
+                            text_bytes=args.n, seed=21, path=hc.HC_TUNE_SINGLE)
             torch.cuda.synchronize(dev)
             if args.tuner_table:
                 tuner.save(args.tuner_table)
@@ -318,15 +378,14 @@ def run_gpu(args, rank, world, local_rank):
     pos_bytes = 8 if args.pos64 else 4
 
     # ---- inputs
-    texts_np = {s: hi.sweep_text(s, args.n) for s in sigmas}
     texts = {s: torch.from_numpy(t).to(dev) for s, t in texts_np.items()}
 
     def make_cells(kind):
         out = {}
         for s, m in grid:
-            pats = hi.sweep_patterns(texts_np[s], s, m, args.patterns)
+            pats = patterns[(s, m)]
             if kind == "tuned":
-                e = tuner.lookup(s, m)
+                e = tuner.lookup(tune_sigma[s], m)
                 q, alpha = e["q"], e["alpha"]
                 opts = hc.SearchOpts(lane_bytes=e["lane_bytes"], mode=e["mode"], pos32=pos32)
             else:
@@ -522,7 +581,7 @@ def run_gpu(args, rank, world, local_rank):
     traffic, traffic_rec = recorded_traffic(dominant)
 
     line = {
-        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "metric": metric_for(args), "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic", "config": workload_config(args),
@@ -554,6 +613,9 @@ def run_gpu(args, rank, world, local_rank):
     if paper is not None:
         line["paper_params"] = paper
         line["tune_s"] = round(tune_s, 2)
+    if args.workload == "skewed":
+        line["config"]["sigma_eff"] = {str(s): round(skew_sigma_eff(texts_np[s]), 2) for s in sigmas}
+        line["config"]["tuner_sigma"] = {str(s): v for s, v in tune_sigma.items()}
 
     # ---- end to end through the synchronous C-ABI call, host buffers
     if not args.no_e2e:

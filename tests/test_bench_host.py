@@ -1,0 +1,66 @@
+"""Host logic of bench.py (no GPU): the workloads' inputs and descriptions,
+the kernel family a search runs, and the effective alphabet size used to
+read the tuner's table for the skewed text."""
+import types
+
+import numpy as np
+import pytest
+
+import bench
+import hc_inputs as hi
+
+
+def _args(**kw):
+    d = dict(workload="sweep", n=1 << 16, skew_n=1 << 16, cells="", params="tuned", eager=False,
+             pos64=False, patterns=3)
+    d.update(kw)
+    return types.SimpleNamespace(**d)
+
+
+def test_sweep_inputs_cover_every_cell():
+    texts, grid, pats = bench.workload_inputs(_args(), 3)
+    assert sorted(texts) == sorted(hi.SWEEP_SIGMAS)
+    assert grid == [(s, m) for s in hi.SWEEP_SIGMAS for m in hi.SWEEP_MS]
+    for (s, m), ps in pats.items():
+        assert len(ps) == 3 and all(p.size == m for p in ps)
+        assert set(np.unique(texts[s])) <= set(hi.alphabet(s))
+
+
+def test_cells_option_limits_the_texts():
+    texts, grid, pats = bench.workload_inputs(_args(cells="4:16,95:2"), 2)
+    assert grid == [(4, 16), (95, 2)] and sorted(texts) == [4, 95]
+
+
+def test_skewed_inputs_are_the_markov_text():
+    a = _args(workload="skewed")
+    texts, grid, pats = bench.workload_inputs(a, 2)
+    assert list(texts) == [bench.SKEW_KEY]
+    y = texts[bench.SKEW_KEY]
+    assert y.size == a.skew_n and np.array_equal(y, hi.skew_text(a.skew_n))
+    assert grid == [(bench.SKEW_KEY, m) for m in hi.SKEW_MS]
+    for (_, m), ps in pats.items():
+        for p in ps:                       # every pattern is copied from the text
+            assert (np.lib.stride_tricks.sliding_window_view(y, m) == p).all(axis=1).any()
+    cfg = bench.workload_config(a)
+    assert cfg["workload"] == "plain HC, skewed text" and cfg["ms"] == list(hi.SKEW_MS)
+    assert bench.metric_for(a) == bench.SKEW_METRIC and bench.metric_for(_args()) == bench.METRIC
+
+
+def test_sigma_eff_closed_forms():
+    # uniform over k symbols: exactly k when every symbol is equally frequent
+    for k in (1, 2, 4, 20, 95):
+        y = np.tile(hi.alphabet(k), 1000)
+        assert bench.skew_sigma_eff(y) == pytest.approx(k)
+    # two symbols with frequencies 3/4, 1/4: 1 / (9/16 + 1/16) = 1.6
+    y = np.array([0, 0, 0, 1] * 1000, dtype=np.uint8)
+    assert bench.skew_sigma_eff(y) == pytest.approx(1.6)
+    # the skewed text is far more repetitive than its 60 symbols suggest
+    assert 5.0 < bench.skew_sigma_eff(hi.skew_text(1 << 22)) < 30.0
+
+
+@pytest.mark.parametrize("m,q,mode,fam", [(4, 4, 0, "scan_dense"), (16, 6, 0, "scan_staged"),
+                                          (1024, 8, 0, "scan_direct"), (256, 4, 0, "scan_direct"),
+                                          (199, 1, 0, "scan_staged"), (16, 6, 2, "scan_direct"),
+                                          (8, 8, 1, "scan_staged")])
+def test_scan_family(m, q, mode, fam):
+    assert bench.scan_family(m, q, mode) == fam
