@@ -340,7 +340,11 @@ int hc_check_bounds(uint64_t *violations);
  * batches release memory; one that can never fit completes with
  * HC_ERR_ADMISSION.  Queue order is kept.  Results (counts, positions) are
  * written by the kernels into pinned host memory mapped into the device, so
- * no copy step follows a batch.
+ * no copy step follows a batch.  That memory is not counted in mem_limit:
+ * each of the max_inflight slots holds 8 * (requests + sum of their caps)
+ * bytes for its largest batch so far, kept until hc_server_destroy; a batch
+ * whose results cannot be allocated completes with HC_ERR_NOMEM and the
+ * server carries on.
  *
  * plain = 1 runs each request as one plain search launch (host-built filter,
  * the kernels of hc_search_async) instead: the comparison form.  Otherwise
@@ -374,9 +378,11 @@ typedef struct hc_server_request {
 typedef struct hc_server_result {
     uint64_t id;
     int status;             /* HC_OK; HC_ERR_CAPACITY: count > cap, the first cap
-                               positions kept; HC_ERR_ADMISSION; HC_ERR_TIMEOUT (a
-                               device wait gave up); HC_ERR_CUDA; HC_ERR_STATE
-                               (cancelled by hc_server_destroy) */
+                               positions kept; HC_ERR_ADMISSION; HC_ERR_NOMEM (the
+                               batch's pinned result memory could not be
+                               allocated); HC_ERR_TIMEOUT (a device wait gave
+                               up); HC_ERR_CUDA; HC_ERR_STATE (cancelled by
+                               hc_server_destroy) */
     uint32_t text;
     int q, alpha;           /* the parameters it ran with */
     uint64_t count;         /* total occurrences */
