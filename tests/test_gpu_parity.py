@@ -422,3 +422,58 @@ def test_full_size_skewed_markov_text():
         got = gpu_positions(x, y, q, alpha)
         want = oracle.hc_search(x, y, q, alpha)
         assert np.array_equal(got, want), m
+
+
+# (sigma, m, q, alpha, lane_bytes, mode): cells of the two full-size
+# workloads with the parameters and launch options the autotuner picks for
+# them on GB300 (dense, staged and direct scans)
+BENCH_CELLS = [(2, 2, 2, 12, 8, 3), (4, 16, 6, 12, 68, 1), (20, 32, 2, 9, 124, 1),
+               (95, 1024, 3, 11, 1022, 2), (60, 8, 8, 11, 16, 3), (60, 64, 4, 10, 376, 1),
+               (60, 512, 5, 12, 1016, 2)]
+
+
+def test_full_size_in_the_timed_launch_configuration():
+    """The full-size texts searched as the benchmark times them: the filter
+    resident on the device, uint32 positions, explicit launch options, the
+    search captured in a CUDA graph on a side stream and replayed twice; the
+    positions equal the oracle's in full and nothing around the output is
+    written."""
+    hc = _hc()
+    stream = torch.cuda.Stream()
+    texts = {}
+    for sigma, m, q, alpha, lane_bytes, mode in BENCH_CELLS:
+        if sigma not in texts:
+            texts.clear()
+            y = hi.skew_text() if sigma == 60 else hi.sweep_text(sigma)
+            texts[sigma] = (y, torch.from_numpy(y).cuda())
+        y, y_dev = texts[sigma]
+        x = hi.sweep_patterns(y, sigma, m, count=1)[0]
+        want = oracle.hc_search(x, y, q, alpha)
+        assert want.size >= 1
+        f = hc.hc_preprocess(x, q, alpha)
+        f.to_device()
+        opts = hc.SearchOpts(lane_bytes=lane_bytes, mode=mode, pos32=1)
+        buf = torch.full((want.size + 8,), -7, dtype=torch.int32, device="cuda")
+        pos = buf[1:1 + want.size + 3]
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            hc.hc_search_ex(f, y_dev, pos, cnt, opts, stream=stream)   # warm-up, outside the graph
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            hc.hc_search_ex(f, y_dev, pos, cnt, opts, stream=stream)
+        for _ in range(2):
+            buf.fill_(-7)
+            cnt.zero_()
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                g.replay()
+            stream.synchronize()
+            hc.hc_check_status(stream)
+            assert int(cnt.item()) == want.size, (sigma, m)
+            got = buf.cpu().numpy()
+            assert np.array_equal(got[1:1 + want.size].view(np.uint32).astype(np.uint64), want), (sigma, m)
+            assert got[0] == -7 and (got[1 + want.size:] == -7).all(), (sigma, m)
+        del g
+        f.free()
