@@ -251,10 +251,12 @@ KERNEL_SOURCES = ("paper_2310_15711_gb300/csrc/hc_kernels.cuh", "paper_2310_1571
                   "paper_2310_15711_gb300/csrc/hc_device.cuh")
 
 
-def recorded_traffic(family: str):
+def recorded_traffic(family: str, workload: str = "sweep"):
     """DRAM bytes per launch of a kernel family from the committed ncu record
-    (profiles/traffic.json): None unless it was taken on the current kernel
-    sources.  Returns (bytes per launch, record)."""
+    (profiles/traffic.json; the sweep's records at the top level, another
+    workload's under its name, since a launch's bytes depend on its text):
+    None unless the workload has a record for the family taken on the
+    current kernel sources.  Returns (bytes per launch, record)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -265,7 +267,7 @@ def recorded_traffic(family: str):
     for name in KERNEL_SOURCES:
         with open(os.path.join(ROOT, name), "rb") as f:
             h.update(f.read())
-    ent = rec.get(family)
+    ent = rec.get(family) if workload == "sweep" else rec.get(workload, {}).get(family)
     if not ent or rec.get("source_sha") != h.hexdigest()[:16]:
         return None, None
     return ent.get("dram_bytes_per_launch"), ent
@@ -578,7 +580,7 @@ def run_gpu(args, rank, world, local_rank):
     dom_ms, dom_launches = kernel_times[dominant]
     achieved = fam_bytes.get(dominant, 0.0) * args.steps / (dom_ms / 1e3) / GB if dom_ms else 0.0
     peak, peak_kind = measured_peaks()
-    traffic, traffic_rec = recorded_traffic(dominant)
+    traffic, traffic_rec = recorded_traffic(dominant, args.workload)
 
     line = {
         "metric": metric_for(args), "value": round(value, 2), "unit": UNIT, "n_gpus": world,

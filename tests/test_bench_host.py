@@ -64,3 +64,31 @@ def test_sigma_eff_closed_forms():
                                           (8, 8, 1, "scan_staged")])
 def test_scan_family(m, q, mode, fam):
     assert bench.scan_family(m, q, mode) == fam
+
+
+def test_traffic_record_belongs_to_its_workload(tmp_path, monkeypatch):
+    """A launch's DRAM bytes depend on its text, so a workload only reads its
+    own record; a record taken on other kernel sources reads as None."""
+    import hashlib
+    import json
+    import os
+    root = tmp_path
+    (root / "profiles").mkdir()
+    for name in bench.KERNEL_SOURCES:
+        os.makedirs(root / os.path.dirname(name), exist_ok=True)
+        (root / name).write_bytes(b"kernel " + name.encode())
+    h = hashlib.sha256()
+    for name in bench.KERNEL_SOURCES:
+        h.update((root / name).read_bytes())
+    rec = {"source_sha": h.hexdigest()[:16],
+           "scan_staged": {"dram_bytes_per_launch": 100, "case": "sweep"},
+           "skewed": {"scan_staged": {"dram_bytes_per_launch": 400, "case": "skewed"}}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.recorded_traffic("scan_staged")[0] == 100
+    assert bench.recorded_traffic("scan_staged", "skewed")[0] == 400
+    assert bench.recorded_traffic("scan_dense", "skewed") == (None, None)
+    assert bench.recorded_traffic("scan_dense") == (None, None)
+    rec["source_sha"] = "0" * 16
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.recorded_traffic("scan_staged") == (None, None)
