@@ -38,7 +38,7 @@ def _upload(y: np.ndarray, offset: int = 0):
     n = y.size
     buf = torch.empty(n + offset + 32, dtype=torch.uint8, device="cuda")
     if n:
-        buf[offset:offset + n].copy_(torch.from_numpy(np.ascontiguousarray(y)))
+        buf[offset:offset + n].copy_(torch.from_numpy(np.require(y, requirements=["C", "W"])))
     return buf[offset:offset + n], buf
 
 
