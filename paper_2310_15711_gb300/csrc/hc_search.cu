@@ -202,20 +202,49 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
         }
         if (!filter_passes) cand = 0;
       }
-      if (__ballot_sync(0xffffffffu, cand != 0u) == 0u) continue;
-      uint32_t mbits = 0;
+      const uint32_t cand_lanes = __ballot_sync(0xffffffffu, cand != 0u);
+      if (cand_lanes == 0u) continue;
+      // exact zero-byte test: bit 8k+7 of zg[g] is set iff window w0+4g+k
+      // equals x (bit 7 of a byte set iff the byte is 0)
+      uint32_t zg[4] = {0u, 0u, 0u, 0u};
       if (cand != 0u) {
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          // exact zero-byte test: bit 7 of a byte set iff the byte is 0;
-          // the four flags go to bits 4g .. 4g+3
-          const uint32_t z = ~(((dg[g] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | dg[g] | 0x7f7f7f7fu);
-          mbits |= (((z >> 7) & 0x01010101u) * 0x01020408u >> 24) << (4 * g);
+        for (int g = 0; g < 4; ++g) zg[g] = ~(((dg[g] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | dg[g] | 0x7f7f7f7fu);
+        if (w0 < 0 || w0 + 16 > wins) {
+          // windows outside [0, wins): vm holds the valid ones in window
+          // order; nibble g of vm spread to bits 7, 15, 23, 31 masks zg[g]
+          uint32_t vm = 0xffffu;
+          if (w0 < 0) vm &= 0xffffu << min(-w0, 16);
+          if (w0 + 16 > wins) vm &= 0xffffu >> (16 - (wins - w0));
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            zg[g] &= ((((vm >> (4 * g)) & 0xfu) * 0x00204081u) & 0x01010101u) << 7;
         }
-        // windows outside [0, wins)
-        if (w0 < 0) mbits &= 0xffffu << min(-w0, 16);
-        if (w0 + 16 > wins) mbits &= 0xffffu >> (16 - (wins - w0));
       }
+      if (__popc(cand_lanes) <= 8) {
+        // few lanes with a candidate (occurrences are sparse): when no lane
+        // holds two, each lane's output offset is the number of lanes below
+        // it that hold one -- a single ballot, no scan.  pk has bit 8k+g set
+        // for window w0+4g+k.
+        uint32_t pk = 0;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) pk |= zg[g] >> (7 - g);
+        const uint32_t one = static_cast<uint32_t>(__popc(pk));
+        if (!__any_sync(0xffffffffu, one > 1u)) {
+          const uint32_t holders = __ballot_sync(0xffffffffu, one != 0u);
+          if (store && one != 0u) {
+            const int p = __ffs(pk) - 1;
+            const unsigned long long out = t + static_cast<unsigned long long>(__popc(holders & ((1u << lane) - 1u)));
+            if (out < S) region[out] = rel + static_cast<uint32_t>(w0 + 4 * (p & 7) + (p >> 3));
+          }
+          t += static_cast<unsigned long long>(__popc(holders));
+          continue;
+        }
+      }
+      // general case: the lane's flags in window order (bit i: window w0+i)
+      uint32_t mbits = 0;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) mbits |= ((zg[g] >> 7) * 0x01020408u >> 24) << (4 * g);
       // in-order compaction (lanes in order, a lane's windows in order),
       // written straight to the spill region
       const uint32_t mine = static_cast<uint32_t>(__popc(mbits));
