@@ -487,6 +487,15 @@ int hc_search_noalloc(const hc_filter *f, const uint32_t *F_dev,
  * bounded wait gave up, else HC_OK.  Errors: HC_ERR_CUDA. */
 int hc_check_status(hc_stream_t stream);
 
+/* Self-test of the failure path of the library's device-side waits:
+ * enqueues on `stream` one kernel whose thread waits, with the same bounded
+ * wait every bulk-copy wait of the search kernels uses, on an mbarrier that
+ * nothing completes.  After about 2 s the wait gives up and sets the status
+ * flag, as a copy that never landed would; the kernel then returns.  The
+ * next hc_check_status on that stream returns HC_ERR_TIMEOUT (and clears the
+ * flag); the context stays usable.  Errors: HC_ERR_CUDA. */
+int hc_selftest_wait_timeout(hc_stream_t stream);
+
 /* Number of launches of the library's own kernels issued so far by this
  * process (all devices, all entry points). */
 uint64_t hc_kernel_launches(void);

@@ -97,6 +97,7 @@ SIGNATURES = {
     "hc_server_get_stats": (ctypes.c_int, [_vp, _vp]),
     "hc_server_destroy": (None, [_vp]),
     "hc_check_status": (ctypes.c_int, [_vp]),
+    "hc_selftest_wait_timeout": (ctypes.c_int, [_vp]),
     "hc_check_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
     "hc_mapped_alloc": (ctypes.c_int, [_sz, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "hc_mapped_free": (None, [_vp]),
@@ -675,6 +676,12 @@ def hc_batch_create_tuned(queries, tuner: HCTuner | None) -> HCBatch:
 
 def hc_check_status(stream=None) -> None:
     _check(lib().hc_check_status(_stream_handle(stream)), "hc_check_status")
+
+
+def hc_selftest_wait_timeout(stream=None) -> None:
+    """Enqueues the self-test whose bounded device wait runs out (about 2 s);
+    the next hc_check_status on the stream raises HC_ERR_TIMEOUT."""
+    _check(lib().hc_selftest_wait_timeout(_stream_handle(stream)), "hc_selftest_wait_timeout")
 
 
 def hc_kernel_launches() -> int:
