@@ -726,6 +726,9 @@ def run_batched(args, rank, world, local_rank):
 
     launches0 = hc.hc_kernel_launches()
     bt = hc.hc_batch_create_tuned(queries("tuned"), tuner)
+    # clocks over the timed replays of both batches and the plain launches
+    sampler = ClockSampler(local_rank, interval_ms=max(min(args.clock_ms, 50), 1), enabled=args.clock_ms > 0)
+    sampler.start()
     t_batch = time_batch(bt)
     tuned_params = [bt.params(i) for i in range(len(qrs))]
     bp = hc.hc_batch_create(queries("paper"))
@@ -751,6 +754,7 @@ def run_batched(args, rank, world, local_rank):
             plain_pass()
         e3.record(stream)
     stream.synchronize()
+    clocks = sampler.stop()
     hc.hc_check_status(stream)
     t_plain = e2.elapsed_time(e3) / max(1, args.steps // 2) / 1e3
     same = bool(torch.equal(counts["tuned"], counts["plain"]) and torch.equal(counts["tuned"], counts["paper"]))
@@ -778,7 +782,9 @@ def run_batched(args, rank, world, local_rank):
         "tuner": tuner.entries(),
         "batch_info": bt.info(),
         "gpu_launches_per_step": 3,
+        "gpu_launches": 3 * args.steps,
         "library_launches_total": hc.hc_kernel_launches() - launches0,
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     bt.destroy()
@@ -821,6 +827,8 @@ def run_served(args, rank, world, local_rank):
     torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
     loads = []
+    sampler = ClockSampler(local_rank, interval_ms=max(args.clock_ms, 1), enabled=args.clock_ms > 0)
+    sampler.start()
     for rate in args.served_rates:
         count = max(200, int(rate * args.served_seconds))
         stream = hi.served_requests(texts, count, float(rate), seed=6 + rate)
@@ -897,6 +905,7 @@ def run_served(args, rank, world, local_rank):
     sat["requests"] = nsat
     sat["speedup_vs_plain"] = round(sat["batched"]["req_per_s"] / sat["plain"]["req_per_s"], 3)
     sat["counts_equal"] = sat_counts[0] == sat_counts[1]
+    clocks = sampler.stop()
     top = loads[-1]
     line = {
         "metric": "served HC: aggregate text GB/s at the highest offered load (p50/p99 latency per load)",
@@ -912,6 +921,8 @@ def run_served(args, rank, world, local_rank):
                    "latency": "scheduled arrival -> result copied on the host"},
         "p50_us": top["batched"]["p50_us"], "p99_us": top["batched"]["p99_us"],
         "loads": loads, "saturation": sat, "tune_s": round(tune_s, 2),
+        "gpu_launches": int(sum(ld["batched"]["gpu_launches"] for ld in loads)),
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     tuner.free()
