@@ -163,6 +163,38 @@ def _dev_ptr(t, dtype_bytes=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _nbytes(t) -> int:
+    """Bytes of a text or pattern tensor (the library reads bytes)."""
+    return t.numel() * t.element_size()
+
+
+def _room(buf, entry_bytes: int) -> int:
+    """Entries of `entry_bytes` bytes that fit in an output buffer (a CUDA
+    tensor of any dtype, or a MappedView of int64 slots)."""
+    if isinstance(buf, MappedView):
+        return buf.count * 8 // entry_bytes
+    return buf.numel() * buf.element_size() // entry_bytes
+
+
+def _cap_for(pos_dev, cap, entry_bytes: int) -> int:
+    """The capacity passed to the library: the caller's cap, which must fit
+    in pos_dev, or all of pos_dev (counted in positions of entry_bytes)."""
+    if pos_dev is None:
+        return 0
+    room = _room(pos_dev, entry_bytes)
+    if cap is None:
+        return room
+    cap = int(cap)
+    if cap < 0 or cap > room:
+        raise ValueError(f"cap {cap} does not fit the output buffer ({room} positions of {entry_bytes} bytes)")
+    return cap
+
+
+def _check_count(count_dev):
+    if count_dev is not None and _room(count_dev, 8) < 1:
+        raise ValueError("count_dev must hold one uint64")
+
+
 class MappedView:
     """A run of int64 slots in a MappedBuffer, usable as an output (pos_dev,
     count_dev) of the search calls."""
@@ -291,11 +323,9 @@ def hc_search_async(f: HCFilter, y_dev, pos_dev, count_dev, n: int | None = None
     """hc_search_async: enqueue the search of y_dev (uint8 CUDA tensor) on
     ``stream``; positions go to pos_dev (int64 CUDA tensor holding uint64
     values, or None), the total to count_dev (int64 CUDA tensor, 1 element)."""
-    n = y_dev.numel() if n is None else int(n)
-    if pos_dev is None:
-        cap = 0
-    elif cap is None:
-        cap = pos_dev.numel()
+    n = _nbytes(y_dev) if n is None else int(n)
+    cap = _cap_for(pos_dev, cap, 8)
+    _check_count(count_dev)
     _check(lib().hc_search_async(f.handle, _dev_ptr(y_dev), n, _dev_ptr(pos_dev), int(cap),
                                  _dev_ptr(count_dev), _stream_handle(stream)),
            "hc_search_async")
@@ -303,12 +333,12 @@ def hc_search_async(f: HCFilter, y_dev, pos_dev, count_dev, n: int | None = None
 
 def hc_search_ex(f: HCFilter, y_dev, pos_dev, count_dev, opts: SearchOpts | None = None,
                  n: int | None = None, cap: int | None = None, stream=None) -> None:
-    """hc_search_ex: hc_search_async with explicit launch options."""
-    n = y_dev.numel() if n is None else int(n)
-    if pos_dev is None:
-        cap = 0
-    elif cap is None:
-        cap = pos_dev.numel()
+    """hc_search_ex: hc_search_async with explicit launch options (with
+    opts.pos32 = 1 the positions are uint32 values and cap counts those)."""
+    n = _nbytes(y_dev) if n is None else int(n)
+    # (a pos32 value other than 0 or 1 is the library's to reject)
+    cap = _cap_for(pos_dev, cap, 4 if opts is not None and opts.pos32 != 0 else 8)
+    _check_count(count_dev)
     _check(lib().hc_search_ex(f.handle, _dev_ptr(y_dev), n, _dev_ptr(pos_dev), int(cap),
                               _dev_ptr(count_dev),
                               ctypes.byref(opts) if opts is not None else None,
@@ -322,11 +352,8 @@ def hc_search(f: HCFilter, x, y_dev, pos_dev=None, cap: int | None = None, strea
     Writes the first min(count, cap) positions into pos_dev.  Raises HCError
     with code HC_ERR_CAPACITY if the count exceeds cap (after writing them),
     unless ``allow_truncated`` is set (e.g. cap = 0 to size a buffer)."""
-    n = y_dev.numel() if n is None else int(n)
-    if pos_dev is None:
-        cap = 0
-    elif cap is None:
-        cap = pos_dev.numel()
+    n = _nbytes(y_dev) if n is None else int(n)
+    cap = _cap_for(pos_dev, cap, 8)
     xb = _bytes_arg(x)
     cnt = _sz()
     xbuf = ctypes.create_string_buffer(xb, len(xb))
@@ -353,11 +380,9 @@ def hc_search_noalloc(f: HCFilter, F_dev, x_dev, y_dev, pos_dev, count_dev,
     """hc_search_noalloc: the search with every buffer supplied by the caller
     (F_dev: the filter's words, x_dev: the pattern, both on the device); the
     library allocates nothing."""
-    n = y_dev.numel() if n is None else int(n)
-    if pos_dev is None:
-        cap = 0
-    elif cap is None:
-        cap = pos_dev.numel()
+    n = _nbytes(y_dev) if n is None else int(n)
+    cap = _cap_for(pos_dev, cap, 8)
+    _check_count(count_dev)
     _check(lib().hc_search_noalloc(f.handle, _dev_ptr(F_dev), _dev_ptr(x_dev), _dev_ptr(y_dev), n,
                                    _dev_ptr(pos_dev), int(cap), _dev_ptr(count_dev),
                                    _stream_handle(stream)), "hc_search_noalloc")
@@ -458,14 +483,14 @@ class HCBatch:
         for i, d in enumerate(queries):
             pos = d.get("pos_dev")
             arr[i].x_dev = _dev_ptr(d["x_dev"])
-            arr[i].m = d["x_dev"].numel()
+            arr[i].m = _nbytes(d["x_dev"])
             arr[i].y_dev = _dev_ptr(d["y_dev"])
-            arr[i].n = d["y_dev"].numel() if "n" not in d else int(d["n"])
+            arr[i].n = _nbytes(d["y_dev"]) if "n" not in d else int(d["n"])
             arr[i].q = int(d.get("q", 0))
             arr[i].alpha = int(d.get("alpha", 0))
             arr[i].sigma = int(d.get("sigma", 0))
             arr[i].pos_dev = _dev_ptr(pos) if pos is not None else None
-            arr[i].cap = int(d.get("cap", pos.numel() if pos is not None else 0))
+            arr[i].cap = _cap_for(pos, d.get("cap"), 8)
             arr[i].count_dev = _dev_ptr(d["count_dev"])
             arr[i].lane_bytes = int(d.get("lane_bytes", 0))
             arr[i].mode = int(d.get("mode", 0))
@@ -580,7 +605,7 @@ class HCServer:
         tid = ctypes.c_uint32()
         if hasattr(y, "is_cuda") and y.is_cuda:
             self._keep.append(y)
-            _check(lib().hc_server_add_text(self.handle, _dev_ptr(y), y.numel(), 1, int(sigma),
+            _check(lib().hc_server_add_text(self.handle, _dev_ptr(y), _nbytes(y), 1, int(sigma),
                                             ctypes.byref(tid)), "hc_server_add_text")
         else:
             b = _bytes_arg(y)

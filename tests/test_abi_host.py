@@ -90,3 +90,25 @@ def test_check_bounds_refused_in_the_regular_build():
     assert hc.lib().hc_check_bounds(ctypes.byref(v)) == hc.HC_ERR_STATE
     assert v.value == 0
     assert hc.lib().hc_check_bounds(None) == hc.HC_ERR_ARG
+
+
+def test_output_capacity_is_counted_in_bytes():
+    """The binding derives a search's capacity from the output buffer's bytes
+    and the position width (8, or 4 with uint32 positions), and refuses a cap
+    the buffer cannot hold, so a narrow buffer is never overrun."""
+    import torch
+    hc = pytest.importorskip("paper_2310_15711_gb300")
+    i64 = torch.zeros(10, dtype=torch.int64)
+    i32 = torch.zeros(10, dtype=torch.int32)
+    u8 = torch.zeros(64, dtype=torch.uint8)
+    assert hc._cap_for(i64, None, 8) == 10 and hc._cap_for(i64, None, 4) == 20
+    assert hc._cap_for(i32, None, 8) == 5 and hc._cap_for(i32, None, 4) == 10
+    assert hc._cap_for(u8, None, 8) == 8 and hc._cap_for(u8[2:34], 4, 8) == 4
+    assert hc._cap_for(None, 123, 8) == 0
+    for buf, cap, width in ((i32, 6, 8), (i64, 21, 4), (u8, 9, 8), (i64, -1, 8)):
+        with pytest.raises(ValueError):
+            hc._cap_for(buf, cap, width)
+    with pytest.raises(ValueError):
+        hc._check_count(torch.zeros(4, dtype=torch.uint8))
+    hc._check_count(torch.zeros(1, dtype=torch.int64))
+    assert hc._nbytes(torch.zeros(3, dtype=torch.int32)) == 12
