@@ -82,6 +82,12 @@ def parse_args():
     ap.add_argument("--clock-ms", type=int, default=200,
                     help="nvidia-smi sampling interval during the timed region (0: no sampling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="sweep only: skip the skewed, batched and served sub-objects")
+    ap.add_argument("--extra-patterns", type=int, default=20,
+                    help="patterns per m of the skewed sub-object")
+    ap.add_argument("--extra-served-seconds", type=float, default=1.0,
+                    help="seconds per offered load of the served sub-object")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", choices=["sweep", "skewed", "batched", "served"], default="sweep",
@@ -247,8 +253,27 @@ def scan_family(m: int, q: int, mode: int = 0) -> str:
     return "scan_staged"
 
 
+def dense_single_pass(opts, m: int) -> bool:
+    """Whether the library runs a dense (m = q) search as its single-pass
+    kernel: the same rule as its planner (chunks of 256 * L window starts,
+    L even, tiles of at most 64 steps of 512 windows, staging buffers and
+    step masks within the 227 KB of shared memory per block)."""
+    if opts is not None and getattr(opts, "single_pass", 0) < 0:
+        return False
+    lane = opts.lane_bytes if opts is not None and opts.lane_bytes else 8
+    stages = opts.stages if opts is not None and opts.stages else 2
+    ls = max(2, (lane + 1) & ~1)
+    spc = ls // 2
+    want = opts.tile_steps if opts is not None and getattr(opts, "tile_steps", 0) else 32
+    tc = max(1, -(-want // spc))
+    if spc * tc > 64:
+        return False
+    stage = ((16 + 256 * ls + m - 1 + 15) & ~15) + 32
+    return 8 * stages * stage + 8 * spc * tc * 64 + 1024 <= 227 * 1024
+
+
 KERNEL_SOURCES = ("paper_2310_15711_gb300/csrc/hc_kernels.cuh", "paper_2310_15711_gb300/csrc/hc_search.cu",
-                  "paper_2310_15711_gb300/csrc/hc_device.cuh")
+                  "paper_2310_15711_gb300/csrc/hc_device.cuh", "paper_2310_15711_gb300/csrc/hc_dense.cu")
 
 
 def recorded_traffic(family: str, workload: str = "sweep"):
@@ -564,8 +589,12 @@ def run_gpu(args, rank, world, local_rank):
         n = texts[s].numel()
         occ = float(cnt[ci].sum())
         fam = scan_family(m, q, opts.mode if opts is not None else 0)
-        fam_bytes[fam] = fam_bytes.get(fam, 0.0) + n * args.patterns + 4 * occ
-        fam_bytes["emit"] = fam_bytes.get("emit", 0.0) + (4 + pos_bytes) * occ
+        if fam == "scan_dense" and dense_single_pass(opts, m):
+            # one kernel reads the text and writes each position once
+            fam_bytes[fam] = fam_bytes.get(fam, 0.0) + n * args.patterns + pos_bytes * occ
+        else:
+            fam_bytes[fam] = fam_bytes.get(fam, 0.0) + n * args.patterns + 4 * occ
+            fam_bytes["emit"] = fam_bytes.get("emit", 0.0) + (4 + pos_bytes) * occ
         cell_s = cell_ms[ci] / 1e3
         # algorithmic DRAM bytes of the cell's searches: the text once (every
         # byte is read when the whole text is staged; direct-mode cells read
@@ -633,8 +662,6 @@ def run_gpu(args, rank, world, local_rank):
         # the paper's own setting: one core
         one = cpu_baseline(texts_np, {k: v[0] for k, v in cells.items()}, args.cpu_seconds / 3, 1)
         line["cpu_baseline"]["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     for key in keys:
         for f in cells[key][1]:
             f.free()
@@ -643,6 +670,7 @@ def run_gpu(args, rank, world, local_rank):
                 f.free()
     if tuner is not None:
         tuner.free()
+    return line if rank == 0 else None
 
 
 BATCH_TUNE_MS = (4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512)
@@ -745,18 +773,36 @@ def run_batched(args, rank, world, local_rank):
             hc.hc_search_async(filters[i], ybuf[offs[i]:offs[i] + qr.n], pos["plain"][pofs[i]:pofs[i + 1]],
                                counts["plain"][i:i + 1], stream=stream)
 
+    # the plain arm as the batch is timed: all its launches captured in one
+    # CUDA graph and replayed (the device runs them back to back, whatever
+    # the host does); the eager enqueue loop is reported beside it
     with torch.cuda.stream(stream):
         plain_pass()
-        stream.synchronize()
+    stream.synchronize()
+    g_plain = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_plain, stream=stream):
+        plain_pass()
+    nplain = max(1, args.steps // 2)
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            g_plain.replay()
         e2, e3 = ev(), ev()
         e2.record(stream)
-        for _ in range(max(1, args.steps // 2)):
-            plain_pass()
+        for _ in range(nplain):
+            g_plain.replay()
         e3.record(stream)
+        stream.synchronize()
+        e4, e5 = ev(), ev()
+        e4.record(stream)
+        for _ in range(nplain):
+            plain_pass()
+        e5.record(stream)
     stream.synchronize()
     clocks = sampler.stop()
     hc.hc_check_status(stream)
-    t_plain = e2.elapsed_time(e3) / max(1, args.steps // 2) / 1e3
+    del g_plain
+    t_plain = e2.elapsed_time(e3) / nplain / 1e3
+    t_plain_eager = e4.elapsed_time(e5) / nplain / 1e3
     same = bool(torch.equal(counts["tuned"], counts["plain"]) and torch.equal(counts["tuned"], counts["paper"]))
     nq_changed = sum(1 for i, qr in enumerate(qrs)
                      if (tuned_params[i]["q"], tuned_params[i]["alpha"]) != (qr.q, qr.alpha))
@@ -776,7 +822,10 @@ def run_batched(args, rank, world, local_rank):
         "queries_retuned": nq_changed,
         "plain_launch_GBps": round(text_bytes / t_plain / GB, 2),
         "plain_launch_ms": round(t_plain * 1e3, 3),
+        "plain_launch": "one hc_search_async per query, all captured in one CUDA graph and replayed",
         "speedup_vs_plain": round(t_plain / t_batch, 3),
+        "plain_eager_GBps": round(text_bytes / t_plain_eager / GB, 2),
+        "speedup_vs_plain_eager": round(t_plain_eager / t_batch, 3),
         "counts_equal": same,
         "tune_s": round(tune_s, 2),
         "tuner": tuner.entries(),
@@ -786,12 +835,12 @@ def run_batched(args, rank, world, local_rank):
         "library_launches_total": hc.hc_kernel_launches() - launches0,
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
     bt.destroy()
     bp.destroy()
     tuner.free()
     for f in filters:
         f.free()
+    return line
 
 
 SERVED_TUNE_MS = (2, 4, 8, 16, 32, 64, 128, 256, 512, 1024)
@@ -924,8 +973,8 @@ def run_served(args, rank, world, local_rank):
         "gpu_launches": int(sum(ld["batched"]["gpu_launches"] for ld in loads)),
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
     tuner.free()
+    return line
 
 
 def combine_ranks(seconds, units, dist=None, device=None):
@@ -1002,10 +1051,10 @@ def main():
         run_reference(args, rank, world)
         return
     if args.workload == "batched":
-        run_batched(args, rank, world, local_rank)
+        print(json.dumps(run_batched(args, rank, world, local_rank)), flush=True)
         return
     if args.workload == "served":
-        run_served(args, rank, world, local_rank)
+        print(json.dumps(run_served(args, rank, world, local_rank)), flush=True)
         return
     if world > 1:
         import torch
@@ -1013,11 +1062,61 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_gpu(args, rank, world, local_rank)
+        line = run_gpu(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
+    if line is not None and args.workload == "sweep" and world == 1 and not args.no_extras and not args.cells:
+        line.update(other_workloads(args, local_rank))
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def other_workloads(args, local_rank):
+    """The skewed, batched and served configurations, measured in the same
+    run as the sweep (one GPU): a compact object each, with the clocks seen
+    over its own timed region.  Fewer patterns, steps and seconds than their
+    own --workload lines take, so that the default run stays within a few
+    minutes."""
+    import copy
+    out = {}
+    t0 = time.perf_counter()
+    a = copy.copy(args)
+    a.workload, a.patterns, a.no_cpu, a.no_e2e = "skewed", args.extra_patterns, True, True
+    a.steps, a.warmup, a.tuner_table = max(3, min(args.steps, 5)), 3, ""
+    sk = run_gpu(a, 0, 1, local_rank)
+    out["skewed"] = {
+        "metric": sk["metric"], "value": sk["value"], "unit": sk["unit"],
+        "ms_per_step": sk["ms_per_step"], "steps": sk["steps"], "warmup": sk["warmup"],
+        "config": sk["config"], "roofline": sk["roofline"], "m_le_32": sk.get("m_le_32"),
+        "paper_params": sk.get("paper_params"), "kernel_ms_per_step": sk["kernel_ms_per_step"],
+        "gpu_launches": sk["gpu_launches"], "clocks": sk["clocks"],
+        "cells": {k: {"GBps": v["GBps"], "kernel": v["kernel"], "hbm_frac": v["hbm_frac"]}
+                  for k, v in sk["cells"].items()}}
+    a = copy.copy(args)
+    a.workload, a.steps, a.warmup = "batched", 3, 3
+    bt = run_batched(a, 0, 1, local_rank)
+    out["batched"] = {k: bt[k] for k in (
+        "metric", "value", "unit", "ms_per_step", "steps", "queries_per_s", "paper_params_GBps",
+        "plain_launch_GBps", "plain_launch", "speedup_vs_plain", "plain_eager_GBps",
+        "speedup_vs_plain_eager", "counts_equal", "gpu_launches", "clocks")}
+    out["batched"]["config"] = bt["config"]
+    a = copy.copy(args)
+    a.workload, a.served_seconds, a.served_backlog = "served", args.extra_served_seconds, 20000
+    sv = run_served(a, 0, 1, local_rank)
+    out["served"] = {
+        "metric": sv["metric"], "value": sv["value"], "unit": sv["unit"],
+        "p50_us": sv["p50_us"], "p99_us": sv["p99_us"], "config": sv["config"],
+        "loads": [{"offered_req_per_s": ld["offered_req_per_s"], "requests": ld["requests"],
+                   "counts_equal": ld["counts_equal"],
+                   "batched": {k: ld["batched"][k] for k in ("p50_us", "p99_us", "achieved_req_per_s", "GBps",
+                                                             "mean_batch", "gpu_launches")},
+                   "plain": {k: ld["plain"][k] for k in ("p50_us", "p99_us", "achieved_req_per_s", "GBps")}}
+                  for ld in sv["loads"]],
+        "saturation": sv["saturation"], "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"]}
+    out["other_workloads_wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 if __name__ == "__main__":

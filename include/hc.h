@@ -153,6 +153,15 @@ typedef struct hc_search_opts {
     int pos32;              /* 1: positions written as uint32 (pos_dev holds cap
                                uint32 values, 4-byte aligned; needs
                                n - m + 1 <= 2^32); 0: uint64 */
+    int single_pass;        /* dense mode: 0 or 1 -- one kernel writes the
+                               positions in text order as it goes (tiles
+                               claimed in order, counts of earlier tiles by a
+                               look-back), after a small kernel that zeroes
+                               its tile table; -1 -- spill regions and a
+                               second kernel (emit) */
+    int tile_steps;         /* single pass: window steps of 512 per tile
+                               (1..64, rounded up to whole chunks);
+                               0 = automatic */
 } hc_search_opts;
 
 /* hc_search_ex: hc_search_async with explicit launch options (opts may be
@@ -453,11 +462,11 @@ void hc_server_destroy(hc_server *s);
 
 /* ------------------------------------------------------------------------
  * hc_search_noalloc: the search of hc_search_async for callers that cannot
- * allocate device memory -- e.g. code running while a CUDA graph is captured
- * on its stream, applications whose device memory is planned in full by
- * their own allocator or arena, or latency-critical paths that must not
- * enter an allocator.  The paper has no counterpart: this is an interface of
- * this library only.
+ * allocate device memory -- e.g. applications whose device memory is
+ * planned in full by their own allocator or arena (a hidden cudaMalloc can
+ * exceed the plan, and cudaFree synchronises the device), or latency-critical
+ * paths that must not enter an allocator.  The paper has no counterpart: this
+ * is an interface of this library only.
  *
  * It allocates nothing (no cudaMalloc, cudaFree or pool allocation): the
  * caller passes every buffer -- F_dev, the filter's 2^alpha words as returned

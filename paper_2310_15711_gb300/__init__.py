@@ -168,6 +168,18 @@ def _nbytes(t) -> int:
     return t.numel() * t.element_size()
 
 
+def _text_len(y_dev, n) -> int:
+    """The text length passed to the library: all of y_dev, or the caller's
+    n, which must not exceed the bytes of y_dev (the kernels read n bytes)."""
+    have = _nbytes(y_dev) if y_dev is not None else 0
+    if n is None:
+        return have
+    n = int(n)
+    if n < 0 or n > have:
+        raise ValueError(f"n = {n} does not fit the text buffer ({have} bytes)")
+    return n
+
+
 def _room(buf, entry_bytes: int) -> int:
     """Entries of `entry_bytes` bytes that fit in an output buffer (a CUDA
     tensor of any dtype, or a MappedView of int64 slots)."""
@@ -258,12 +270,14 @@ class SearchOpts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("lane_bytes", ctypes.c_int),
                 ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("mode", ctypes.c_int), ("spill_entries", ctypes.c_uint64),
-                ("speculate", ctypes.c_int), ("pos32", ctypes.c_int)]
+                ("speculate", ctypes.c_int), ("pos32", ctypes.c_int),
+                ("single_pass", ctypes.c_int), ("tile_steps", ctypes.c_int)]
 
     def __init__(self, lane_bytes=0, stages=0, ctas_per_sm=0, spill_entries=0, mode=0,
-                 speculate=0, pos32=0):
+                 speculate=0, pos32=0, single_pass=0, tile_steps=0):
         super().__init__(ctypes.sizeof(SearchOpts), int(lane_bytes), int(stages),
-                         int(ctas_per_sm), int(mode), int(spill_entries), int(speculate), int(pos32))
+                         int(ctas_per_sm), int(mode), int(spill_entries), int(speculate), int(pos32),
+                         int(single_pass), int(tile_steps))
 
 
 class HCFilter:
@@ -323,7 +337,7 @@ def hc_search_async(f: HCFilter, y_dev, pos_dev, count_dev, n: int | None = None
     """hc_search_async: enqueue the search of y_dev (uint8 CUDA tensor) on
     ``stream``; positions go to pos_dev (int64 CUDA tensor holding uint64
     values, or None), the total to count_dev (int64 CUDA tensor, 1 element)."""
-    n = _nbytes(y_dev) if n is None else int(n)
+    n = _text_len(y_dev, n)
     cap = _cap_for(pos_dev, cap, 8)
     _check_count(count_dev)
     _check(lib().hc_search_async(f.handle, _dev_ptr(y_dev), n, _dev_ptr(pos_dev), int(cap),
@@ -335,7 +349,7 @@ def hc_search_ex(f: HCFilter, y_dev, pos_dev, count_dev, opts: SearchOpts | None
                  n: int | None = None, cap: int | None = None, stream=None) -> None:
     """hc_search_ex: hc_search_async with explicit launch options (with
     opts.pos32 = 1 the positions are uint32 values and cap counts those)."""
-    n = _nbytes(y_dev) if n is None else int(n)
+    n = _text_len(y_dev, n)
     # (a pos32 value other than 0 or 1 is the library's to reject)
     cap = _cap_for(pos_dev, cap, 4 if opts is not None and opts.pos32 != 0 else 8)
     _check_count(count_dev)
@@ -352,7 +366,7 @@ def hc_search(f: HCFilter, x, y_dev, pos_dev=None, cap: int | None = None, strea
     Writes the first min(count, cap) positions into pos_dev.  Raises HCError
     with code HC_ERR_CAPACITY if the count exceeds cap (after writing them),
     unless ``allow_truncated`` is set (e.g. cap = 0 to size a buffer)."""
-    n = _nbytes(y_dev) if n is None else int(n)
+    n = _text_len(y_dev, n)
     cap = _cap_for(pos_dev, cap, 8)
     xb = _bytes_arg(x)
     cnt = _sz()
@@ -380,9 +394,14 @@ def hc_search_noalloc(f: HCFilter, F_dev, x_dev, y_dev, pos_dev, count_dev,
     """hc_search_noalloc: the search with every buffer supplied by the caller
     (F_dev: the filter's words, x_dev: the pattern, both on the device); the
     library allocates nothing."""
-    n = _nbytes(y_dev) if n is None else int(n)
+    n = _text_len(y_dev, n)
     cap = _cap_for(pos_dev, cap, 8)
     _check_count(count_dev)
+    prm = f.params()
+    if F_dev is None or _nbytes(F_dev) < 4 << prm["alpha"]:
+        raise ValueError(f"F_dev must hold the filter's {1 << prm['alpha']} words")
+    if x_dev is None or _nbytes(x_dev) < prm["m"]:
+        raise ValueError(f"x_dev must hold the pattern's {prm['m']} bytes")
     _check(lib().hc_search_noalloc(f.handle, _dev_ptr(F_dev), _dev_ptr(x_dev), _dev_ptr(y_dev), n,
                                    _dev_ptr(pos_dev), int(cap), _dev_ptr(count_dev),
                                    _stream_handle(stream)), "hc_search_noalloc")
@@ -485,7 +504,7 @@ class HCBatch:
             arr[i].x_dev = _dev_ptr(d["x_dev"])
             arr[i].m = _nbytes(d["x_dev"])
             arr[i].y_dev = _dev_ptr(d["y_dev"])
-            arr[i].n = _nbytes(d["y_dev"]) if "n" not in d else int(d["n"])
+            arr[i].n = _text_len(d["y_dev"], d.get("n"))
             arr[i].q = int(d.get("q", 0))
             arr[i].alpha = int(d.get("alpha", 0))
             arr[i].sigma = int(d.get("sigma", 0))

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     hc_batch_emit_kernel(const SearchArgs* args, const EmitTile* etiles) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(16) SearchArgs sa;

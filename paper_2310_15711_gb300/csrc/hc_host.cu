@@ -30,7 +30,7 @@ std::unordered_map<int, DeviceInfo> g_dev_info;
 std::atomic<uint64_t> g_launches{0};
 
 const char* const kKindNames[kNumKinds] = {"scan_staged", "scan_direct", "scan_dense",
-                                           "emit", "preprocess", "batch"};
+                                           "emit", "preprocess", "batch", "lb_init"};
 
 namespace {
 std::atomic<bool> g_timing_on{false};

@@ -61,7 +61,8 @@ enum KernelKind {
   kKindEmit = 3,
   kKindPreprocess = 4,
   kKindBatch = 5,
-  kNumKinds = 6
+  kKindInit = 6,
+  kNumKinds = 7
 };
 extern const char* const kKindNames[kNumKinds];
 
@@ -132,10 +133,20 @@ struct SearchPlan {
   bool spec = false;              // warp-speculative HC (staged/direct kinds)
   bool pos32 = false;             // positions written as uint32
   size_t ws_bytes = 0;            // workspace bytes (device), no zeroing needed
+  // single-pass dense form: an init kernel zeroes the tile ticket and the
+  // tile descriptors, then the scan writes positions and the count itself
+  // (no spill regions, no emit kernel)
+  bool single_pass = false;
+  KernelFn init = nullptr;
+  int tile_chunks = 0, flag_steps = 0;
+  unsigned long long max_tiles = 0;  // descriptors in the workspace
 };
 
 int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, int dev,
                 SearchPlan* out);
+// The single-pass dense scan for a given q and its init kernel (hc_dense.cu).
+KernelFn dense_single_pass_kernel_for_q(int q);
+KernelFn single_pass_init_kernel();
 // Device address of the library's status word on the current device.
 unsigned int* status_word();
 int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,

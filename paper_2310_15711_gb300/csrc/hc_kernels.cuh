@@ -23,6 +23,8 @@ constexpr int kDirectShift = 200;           // shifts this long skip most 32-byt
 constexpr int kEmitSplit = 2;               // CTAs of the emit kernel per record group
 constexpr int kMaxEmitGroup = 64;           // records per emit record group, at most
 constexpr int kEmitUnits = 8;               // 8-byte region loads in flight per emit thread
+constexpr int kSinglePassMaxSteps = 64;     // 512-window steps per single-pass tile (a u64 of flags)
+constexpr int kSinglePassTileSteps = 32;    // default steps per single-pass tile
 
 
 // Bytes of one staging buffer: head (< 16) + C + m - 1 bytes of text rounded
@@ -68,6 +70,15 @@ struct SearchArgs {
   // weights w0, bytes [g0, q) with weights w1, scaled by 2^(s*g0)
   uint32_t w0, w1;
   int g0;
+  // single-pass dense form (m = q): tiles of tile_chunks consecutive chunks
+  // are claimed in order from *lb_ticket; lb_desc[t] carries tile t's
+  // aggregate or inclusive count (see hc_dense.cu); flag_steps is the number
+  // of 512-window steps per tile (the per-warp flag buffer in shared memory)
+  unsigned int* lb_ticket;
+  unsigned long long* lb_desc;
+  unsigned long long num_tiles;
+  int tile_chunks;
+  int flag_steps;
 };
 
 // ---------------------------------------------------------------------------
@@ -80,14 +91,14 @@ struct SearchArgs {
 // or a split after 2-4 bytes), and the value equals the Horner evaluation of
 // Eq. 3 exactly, since no partial sum exceeds 32 bits.
 // `lo` holds bytes 0-3 of the q-gram, `hi` bytes 4-7 (little-endian).
+// When q <= g0 the second group is empty and w1 = 0, so the second dot
+// product adds nothing: the evaluation has no branch.
 template <int Q>
 __device__ __forceinline__ uint32_t hash_bytes(uint32_t lo, uint32_t hi, const SearchArgs& a) {
   uint32_t v = __dp4a(lo, a.w0, 0u);
   if constexpr (Q > 1) {
-    if (Q > a.g0) {
-      const uint32_t rest = __funnelshift_rc(lo, hi, 8u * static_cast<uint32_t>(a.g0));
-      v += __dp4a(rest, a.w1, 0u) << (a.s * a.g0);
-    }
+    const uint32_t rest = __funnelshift_rc(lo, hi, 8u * static_cast<uint32_t>(a.g0));
+    v += __dp4a(rest, a.w1, 0u) << (a.s * a.g0);
   }
   return v & a.mask;
 }
@@ -286,6 +297,8 @@ __device__ __forceinline__ int warp_scan_chunk(const uint8_t* base, int head, in
 
 // Walk steps a lane takes on its own before handing the window to its warp.
 constexpr int kShallowSteps = 3;
+// First tests a lane evaluates together (see scan_segment).
+constexpr int kFirstTests = 4;
 
 // HC (Fig. 5 left) over the window starts [lo, hi) of a chunk, one segment
 // per thread; chunk-relative text byte k is base[head + k].  Returns the
@@ -316,12 +329,36 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
   uint32_t dz = 0;                 // F word of the q-gram ending at dj
   while (true) {
     while (!deep && e < e_end) {
-      // first test: the q-gram ending at the window end
-      uint32_t v = qgram_hash<Q, STAGED>(base, head + e - Q + 1, a);
-      uint32_t z = Fs[v];
-      if (z == 0) {
-        e += shift;
-        continue;
+      // first tests of the next kFirstTests windows of the miss sequence e,
+      // e + shift, ... at once (independent loads, one branch per run): each
+      // window whose end q-gram hits an empty word is shifted past, as the
+      // sequential loop does; the first window that hits a non-empty word
+      // goes on to the back-walk.  Windows past the segment take no part
+      // (their test reads window e's q-gram and is discarded).
+      uint32_t v = 0, z = 0;
+      {
+        uint32_t vu[kFirstTests], zu[kFirstTests];
+#pragma unroll
+        for (int u = 0; u < kFirstTests; ++u) {
+          const int ek = e + u * shift;
+          const bool in = u == 0 || ek < e_end;
+          vu[u] = qgram_hash<Q, STAGED>(base, head + (in ? ek : e) - Q + 1, a);
+          zu[u] = in ? Fs[vu[u]] : 0u;
+        }
+        int k = kFirstTests;
+#pragma unroll
+        for (int u = kFirstTests - 1; u >= 0; --u) {
+          if (zu[u] != 0u) {
+            k = u;
+            v = vu[u];
+            z = zu[u];
+          }
+        }
+        if (k == kFirstTests) {
+          e += kFirstTests * shift;
+          continue;
+        }
+        e += k * shift;
       }
       // back-walk over the q-grams to the left, each linked to its right one
       int j = e;

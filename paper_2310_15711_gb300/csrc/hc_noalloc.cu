@@ -1,12 +1,11 @@
 // hc_noalloc.cu -- hc_search_noalloc: the search for callers that must not
 // allocate device memory.
 //
-// Some callers cannot let a library allocate: code that runs while a CUDA
-// graph is being captured on its stream (allocation calls break the capture),
-// applications whose device memory is planned in full by their own allocator
-// or arena (a hidden cudaMalloc can exceed the plan, and cudaFree
-// synchronises the device), and latency-critical paths where an allocator
-// round trip is not allowed.  This entry point gives them the same search
+// Some callers cannot let a library allocate: applications whose device
+// memory is planned in full by their own allocator or arena (a hidden
+// cudaMalloc can exceed the plan, and cudaFree synchronises the device), and
+// latency-critical paths where an allocator round trip is not allowed.  This
+// entry point gives them the same search
 // with every buffer provided: the caller passes the filter words and the
 // pattern in device memory, the text, the output positions and the count;
 // the scratch that holds each CTA's occurrences until their output offsets
@@ -26,6 +25,11 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB per device
 constexpr unsigned long long kNoAllocMaxPositions = 2000000ull;
+// The spill form's scratch is at most 32 bytes per record (16 of totals, up
+// to 16 of rounding of its region) plus 4 per held position; records are
+// capped so that any request within kNoAllocMaxPositions fits.
+constexpr unsigned long long kNoAllocMaxRecords =
+    (kNoAllocScratchBytes - 4 * kNoAllocMaxPositions) / 32;
 
 // Scratch of hc_search_noalloc: per-CTA totals and overflow marks, then the
 // per-CTA spill regions.  Every entry the kernels read is written by the
@@ -96,9 +100,18 @@ extern "C" int hc_search_noalloc(const hc_filter* fp, const uint32_t* F_dev, con
   hc_search_opts o{};
   o.struct_size = sizeof o;
   o.spill_entries = std::max<unsigned long long>(held, 1);
+  // one record per warp: at most kNoAllocMaxRecords of them on this device
+  const unsigned long long sms = static_cast<unsigned long long>(device_info(dev).sm_count);
+  o.ctas_per_sm = static_cast<int>(std::max<unsigned long long>(1, kNoAllocMaxRecords / (8 * std::max(sms, 1ull))));
   SearchPlan p;
   rc = plan_search(f, n, cap, &o, dev, &p);
   if (rc != HC_OK) return rc;
+  if (p.single_pass && p.ws_bytes > kNoAllocScratchBytes) {
+    // too many tiles for the scratch (a text of tens of GB): the spill form
+    o.single_pass = -1;
+    rc = plan_search(f, n, cap, &o, dev, &p);
+    if (rc != HC_OK) return rc;
+  }
   if (p.ws_bytes > kNoAllocScratchBytes) {
     char buf[200];
     std::snprintf(buf, sizeof buf,

@@ -56,7 +56,7 @@ __device__ unsigned int g_status;
 // memory.  Occurrences go, in text order, to the warp's spill region; the
 // total to cta_total[w].  No CTA-wide barrier in the loop.
 template <int Q, bool STAGED>
-__global__ void __launch_bounds__(kThreads) hc_scan_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(kThreads, STAGED ? 4 : 5) hc_scan_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
   pdl_launch_dependents();  // the emit kernel may be scheduled; it waits for this grid
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
 // once per group), and kEmitSplit CTAs share each group's copying; the first
 // of them writes the count (last record) and does the re-scans.
 template <int Q>
-__global__ void __launch_bounds__(kThreads) hc_emit_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) hc_emit_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   pdl_wait();  // the scan grid has completed and its records are visible
   emit_group<Q>(a, blockIdx.x / kEmitSplit, blockIdx.x % kEmitSplit, smem);
@@ -442,7 +442,43 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   // most 11 bytes past the last q-gram's first byte (three 32-bit words), the
   // dense kernel at most 20 past the chunk's last window start
   p.stage_bytes = stage_bytes_for(p.C, f->m, kind == HC_MODE_DENSE);
-  if (kind == HC_MODE_DENSE) {
+  const int sp_opt = o ? o->single_pass : 0;
+  const int tile_steps_opt = o ? o->tile_steps : 0;
+  if (sp_opt < -1 || sp_opt > 1) return set_error(HC_ERR_ARG, "hc_search: single_pass out of [-1, 1]");
+  if (tile_steps_opt < 0 || tile_steps_opt > kSinglePassMaxSteps)
+    return set_error(HC_ERR_ARG, "hc_search: tile_steps out of [0, 64]");
+  if (kind == HC_MODE_DENSE && sp_opt >= 0) {
+    // single pass: chunks of a whole number of 512-window steps (L even),
+    // tiles of whole chunks, at most kSinglePassMaxSteps steps per tile
+    const int Ls = std::max(2, (L + 1) & ~1);
+    const int spc = Ls / 2;  // steps per chunk
+    const int want = tile_steps_opt ? tile_steps_opt : kSinglePassTileSteps;
+    const int tc = std::max(1, (want + spc - 1) / spc);
+    if (spc * tc <= kSinglePassMaxSteps) {
+      p.single_pass = true;
+      p.L = Ls;
+      p.C = static_cast<uint32_t>(kThreads) * static_cast<uint32_t>(Ls);
+      p.tile_chunks = tc;
+      p.flag_steps = spc * tc;
+      p.stage_bytes = stage_bytes_for(p.C, f->m, true);
+      p.scan = dense_single_pass_kernel_for_q(f->q);
+      p.init = single_pass_init_kernel();
+      // per warp: its ring of staging buffers and its step masks (u16 per lane)
+      p.smem_scan = size_t(kWarps) * stages * p.stage_bytes + size_t(kWarps) * p.flag_steps * 64;
+      if (p.smem_scan + static_smem(p.scan) > di.smem_optin) p.single_pass = false;
+    } else if (sp_opt == 1) {
+      return set_error(HC_ERR_ARG, "hc_search: single pass needs at most 64 steps of 512 windows per tile");
+    }
+    if (!p.single_pass) {
+      if (sp_opt == 1) return set_error(HC_ERR_ARG, "hc_search: single-pass buffers exceed shared memory");
+      p.L = L;
+      p.C = static_cast<uint32_t>(kThreads) * static_cast<uint32_t>(L);
+      p.stage_bytes = stage_bytes_for(p.C, f->m, true);
+    }
+  } else if (sp_opt == 1) {
+    return set_error(HC_ERR_ARG, "hc_search: single_pass applies to the dense mode only");
+  }
+  if (kind == HC_MODE_DENSE && !p.single_pass) {
     // one ring of `stages` buffers per warp
     p.scan = dense_kernel_for_q(f->q);
     p.smem_scan = fbytes + size_t(kWarps) * stages * p.stage_bytes;
@@ -487,6 +523,21 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   if (o && o->ctas_per_sm > 0) per_sm = std::min(per_sm, o->ctas_per_sm);
 
   const unsigned long long nwin = n - f->m + 1;
+  if (p.single_pass) {
+    // chunk c holds window starts [cC - head, cC - head + C) (head = y mod
+    // 16 < 16); a persistent grid of at most one wave of warps claims tiles
+    const unsigned long long chunks = (nwin + 15 + p.C - 1) / p.C;
+    p.max_tiles = (chunks + p.tile_chunks - 1) / p.tile_chunks;
+    p.num_chunks = chunks;
+    p.grid = std::min<unsigned long long>(static_cast<unsigned long long>(per_sm) * di.sm_count,
+                                          (p.max_tiles + kWarps - 1) / kWarps);
+    p.records = 0;
+    p.emit = nullptr;
+    p.emit_ctas = 0;
+    p.ws_bytes = p.max_tiles * 8 + 16;
+    *out = p;
+    return HC_OK;
+  }
   p.num_chunks = (nwin + p.C - 1) / p.C;
   // one record (total, overflow mark, spill region) per warp, each owning a
   // contiguous range of chunks
@@ -541,8 +592,8 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   a.y = y;
   a.n = n;
   a.nwin = n - f->m + 1;
-  a.F = f->dev_F();
-  a.x = f->dev_x();
+  a.F = f->dev_image ? f->dev_F() : nullptr;
+  a.x = f->dev_image ? f->dev_x() : nullptr;
   a.fwords = static_cast<uint32_t>(f->F.size());
   a.m = static_cast<int>(f->m);
   a.q = f->q;
@@ -552,15 +603,26 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   a.pos = reinterpret_cast<unsigned long long*>(pos);
   a.cap = pos ? cap : 0;
   a.count_out = reinterpret_cast<unsigned long long*>(count_dev);
-  a.cta_total = static_cast<unsigned long long*>(ws);
-  a.cta_overflow = a.cta_total + p.records;
-  a.region = reinterpret_cast<uint32_t*>(a.cta_overflow + p.records);
+  if (p.single_pass) {
+    a.lb_desc = static_cast<unsigned long long*>(ws);
+    a.lb_ticket = reinterpret_cast<unsigned int*>(a.lb_desc + p.max_tiles);
+    a.tile_chunks = p.tile_chunks;
+    a.flag_steps = p.flag_steps;
+  } else {
+    a.cta_total = static_cast<unsigned long long*>(ws);
+    a.cta_overflow = a.cta_total + p.records;
+    a.region = reinterpret_cast<uint32_t*>(a.cta_overflow + p.records);
+  }
   a.region_entries = p.region_entries;
   a.num_chunks = p.num_chunks;
   a.chunks_per_cta = p.chunks_per_cta;
   a.L = p.L;
   a.C = p.C;
   a.head = static_cast<int>(reinterpret_cast<uintptr_t>(y) & 15u);
+  if (p.single_pass) {
+    a.num_chunks = (a.nwin + static_cast<unsigned long long>(a.head) + p.C - 1) / p.C;
+    a.num_tiles = (a.num_chunks + p.tile_chunks - 1) / p.tile_chunks;
+  }
   a.stage_bytes = p.stage_bytes;
   a.x_smem = p.x_smem;
   a.stages = p.stages;
@@ -579,17 +641,33 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   for (int k = 0; k < q - g && k < 4; ++k) a.w1 |= (1u << (s * k)) << (8 * k);
 }
 
-// Enqueues the two kernels of one search with a caller-supplied workspace.
-int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n, uint64_t* pos,
-                   size_t cap, uint64_t* count_dev, void* ws, cudaStream_t stream) {
-  SearchArgs a;
-  fill_args(f, p, y, n, pos, cap, count_dev, ws, &a);
+// Enqueues the kernels of one planned search: scan then emit (PDL), or for
+// the single-pass form init then scan (PDL).
+static int launch_args(const SearchPlan& p, const SearchArgs& a, cudaStream_t stream) {
   if (a.status == nullptr) return set_error(HC_ERR_CUDA, "device status word unavailable");
   const int kind = p.kind == HC_MODE_DENSE ? kKindScanDense
                    : (p.kind == HC_MODE_DIRECT ? kKindScanDirect : kKindScanStaged);
+  cudaError_t e;
+  if (p.single_pass) {
+    const unsigned init_grid = static_cast<unsigned>(
+        std::max<unsigned long long>(1, std::min<unsigned long long>((a.num_tiles + kThreads - 1) / kThreads, 1024)));
+    TimingToken t0 = timing_begin(kKindInit, stream);
+    p.init<<<init_grid, kThreads, 0, stream>>>(a);
+    e = cudaGetLastError();
+    timing_end(t0, stream);
+    if (e != cudaSuccess) return cuda_error(e, "single-pass init launch");
+    TimingToken t1 = timing_begin(kind, stream);
+    e = launch_dependent(p.scan, static_cast<unsigned>(p.grid), kThreads, p.smem_scan, stream,
+                         !t1.active(), a);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    timing_end(t1, stream);
+    g_launches.fetch_add(2);
+    if (e != cudaSuccess) return cuda_error(e, "single-pass scan launch");
+    return HC_OK;
+  }
   TimingToken t0 = timing_begin(kind, stream);
   p.scan<<<static_cast<unsigned>(p.grid), kThreads, p.smem_scan, stream>>>(a);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   timing_end(t0, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
   TimingToken t1 = timing_begin(kKindEmit, stream);
@@ -602,31 +680,24 @@ int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_
   return HC_OK;
 }
 
-// Enqueues the two kernels of one search reading the filter words and the
+// Enqueues the kernels of one search with a caller-supplied workspace.
+int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n, uint64_t* pos,
+                   size_t cap, uint64_t* count_dev, void* ws, cudaStream_t stream) {
+  SearchArgs a;
+  fill_args(f, p, y, n, pos, cap, count_dev, ws, &a);
+  return launch_args(p, a, stream);
+}
+
+// Enqueues the kernels of one search reading the filter words and the
 // pattern from caller-supplied device copies instead of the filter's own.
 int launch_planned_filter_ptrs(const Filter* f, const SearchPlan& p, const uint32_t* F_dev,
                                const uint8_t* x_dev, const uint8_t* y, size_t n, uint64_t* pos,
                                size_t cap, uint64_t* count_dev, void* ws, cudaStream_t stream) {
   SearchArgs a;
   fill_args(f, p, y, n, pos, cap, count_dev, ws, &a);
-  if (a.status == nullptr) return set_error(HC_ERR_CUDA, "device status word unavailable");
   a.F = F_dev;
   a.x = x_dev;
-  const int kind = p.kind == HC_MODE_DENSE ? kKindScanDense
-                   : (p.kind == HC_MODE_DIRECT ? kKindScanDirect : kKindScanStaged);
-  TimingToken t0 = timing_begin(kind, stream);
-  p.scan<<<static_cast<unsigned>(p.grid), kThreads, p.smem_scan, stream>>>(a);
-  cudaError_t e = cudaGetLastError();
-  timing_end(t0, stream);
-  if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
-  TimingToken t1 = timing_begin(kKindEmit, stream);
-  e = launch_dependent(p.emit, static_cast<unsigned>(p.emit_ctas), kThreads, p.smem_emit, stream,
-                       !t1.active(), a);
-  if (e == cudaSuccess) e = cudaGetLastError();
-  timing_end(t1, stream);
-  g_launches.fetch_add(2);
-  if (e != cudaSuccess) return cuda_error(e, "hc_emit_kernel launch");
-  return HC_OK;
+  return launch_args(p, a, stream);
 }
 
 // Enqueues one search; the workspace comes from the library's stream-ordered

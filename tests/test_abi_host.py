@@ -112,3 +112,22 @@ def test_output_capacity_is_counted_in_bytes():
         hc._check_count(torch.zeros(4, dtype=torch.uint8))
     hc._check_count(torch.zeros(1, dtype=torch.int64))
     assert hc._nbytes(torch.zeros(3, dtype=torch.int32)) == 12
+
+
+def test_text_length_must_fit_the_text_buffer():
+    """An explicit text length larger than the text buffer is refused by the
+    binding before any launch (the kernels would read n bytes), for every
+    search entry point: they all take n through _text_len."""
+    import torch
+    hc = pytest.importorskip("paper_2310_15711_gb300")
+    y = torch.zeros(100, dtype=torch.uint8)
+    assert hc._text_len(y, None) == 100 and hc._text_len(y, 100) == 100 and hc._text_len(y, 0) == 0
+    assert hc._text_len(torch.zeros(10, dtype=torch.int32), 40) == 40
+    for bad in (101, -1, 1 << 40):
+        with pytest.raises(ValueError):
+            hc._text_len(y, bad)
+    import inspect
+    src = inspect.getsource(hc)
+    assert "_nbytes(y_dev) if n is None" not in src
+    for fn in (hc.hc_search_async, hc.hc_search_ex, hc.hc_search, hc.hc_search_noalloc):
+        assert "_text_len(y_dev, n)" in inspect.getsource(fn), fn.__name__

@@ -208,9 +208,13 @@ def test_launch_options_and_spill_overflow(opts):
 @pytest.mark.parametrize("opts", [
     dict(mode=3), dict(mode=3, lane_bytes=1), dict(mode=3, lane_bytes=24, stages=2),
     dict(mode=3, lane_bytes=33, spill_entries=10), dict(mode=3, spill_entries=1),
-    dict(mode=3, lane_bytes=5, ctas_per_sm=1, stages=3)])
+    dict(mode=3, lane_bytes=5, ctas_per_sm=1, stages=3),
+    dict(mode=3, single_pass=-1), dict(mode=3, single_pass=-1, lane_bytes=1),
+    dict(mode=3, single_pass=-1, lane_bytes=33, spill_entries=10),
+    dict(mode=3, single_pass=-1, spill_entries=1, stages=3)])
 def test_dense_mode_m_equals_q(opts):
-    """m = q: the warp-cooperative kernel against the oracle, for every q."""
+    """m = q: the warp-cooperative kernels against the oracle, for every q:
+    the single-pass form (the default) and the spill-and-emit form."""
     hc = _hc()
     rng = np.random.default_rng(41)
     for sigma, m, n in [(2, 2, 1_000_003), (4, 4, 600_000), (20, 3, 250_001), (1, 5, 70_000),
@@ -228,6 +232,49 @@ def test_dense_mode_m_equals_q(opts):
             assert int(cnt.item()) == want.size, (sigma, m, opts)
             k = min(cap, want.size)
             assert np.array_equal(pos[:k].cpu().numpy().view(np.uint64), want[:k]), (sigma, m, opts)
+        f.free()
+
+
+@pytest.mark.parametrize("opts", [
+    dict(single_pass=1), dict(single_pass=1, tile_steps=1, lane_bytes=2),
+    dict(single_pass=1, tile_steps=3, lane_bytes=2, stages=4),
+    dict(single_pass=1, tile_steps=64, lane_bytes=4), dict(single_pass=1, lane_bytes=7, stages=3),
+    dict(single_pass=1, ctas_per_sm=1, tile_steps=2), dict(single_pass=1, pos32=1, tile_steps=1, lane_bytes=2),
+    dict(single_pass=1, lane_bytes=16, tile_steps=64)])
+def test_dense_single_pass_tiles_and_edges(opts):
+    """The single-pass dense scan: tiles of 1 to 64 steps (many tiles, so
+    the look-back crosses many descriptors and several rounds of 32), texts
+    from one window to a few MB at every 16-byte offset, every window a
+    match (sigma = 1), capacities from 0 to above the count; the count is
+    exact and the first min(count, cap) positions equal the oracle's, with
+    nothing written past them."""
+    hc = _hc()
+    rng = np.random.default_rng(4242)
+    opts = dict(opts, mode=3)
+    pos32 = opts.get("pos32", 0) == 1
+    cases = [(1, 1, 1), (1, 3, 3), (2, 2, 2), (4, 4, 5), (1, 2, 511), (2, 1, 513), (4, 3, 4096),
+             (1, 4, 70_001), (2, 2, 1_000_003), (4, 5, 777_777), (20, 6, 300_000), (95, 8, 2_500_001),
+             (4, 7, 123_457), (3, 8, 600_000), (2, 1, 3_000_001)]
+    for i, (sigma, m, n) in enumerate(cases):
+        x, y = _case(rng, sigma, n, m, plant=int(rng.integers(0, 60)))
+        want = oracle.hc_search(x, y, m, 12)
+        offset = i % 16
+        y_dev, keep = _upload(y, offset=offset)
+        f = hc.hc_preprocess(x, m, 12)
+        for cap in sorted({0, 1, want.size // 2, want.size, want.size + 2}):
+            dt = torch.int32 if pos32 else torch.int64
+            buf = torch.full((cap + 2,), -7, dtype=dt, device="cuda")
+            pos = buf[1:1 + cap] if cap else None
+            cnt = torch.full((1,), -5, dtype=torch.int64, device="cuda")
+            hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(**opts), cap=cap)
+            torch.cuda.synchronize()
+            hc.hc_check_status()
+            assert int(cnt.item()) == want.size, (sigma, m, n, offset, opts, cap)
+            k = min(cap, want.size)
+            got = buf.cpu().numpy()
+            vals = got[1:1 + k].view(np.uint32).astype(np.uint64) if pos32 else got[1:1 + k].view(np.uint64)
+            assert np.array_equal(vals, want[:k]), (sigma, m, n, offset, opts, cap)
+            assert got[0] == -7 and (got[1 + k:] == -7).all(), (sigma, m, n, offset, opts, cap)
         f.free()
 
 
@@ -393,7 +440,8 @@ def test_search_opts_rejected_when_out_of_range():
     f = hc.hc_preprocess(b"ACGTACGT", 4, 12)
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     for bad in (dict(lane_bytes=5000), dict(stages=5), dict(stages=1), dict(mode=3),
-                dict(mode=7)):
+                dict(mode=7), dict(single_pass=2), dict(single_pass=-2), dict(tile_steps=65),
+                dict(tile_steps=-1), dict(mode=1, single_pass=1)):
         with pytest.raises(hc.HCError) as ei:
             hc.hc_search_ex(f, y_dev, None, cnt, hc.SearchOpts(**bad))
         assert ei.value.code == hc.HC_ERR_ARG
