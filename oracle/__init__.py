@@ -50,7 +50,7 @@ def build(force: bool = False) -> str:
              or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-std=c99", "-Wall", "-shared", "-fPIC",
+        subprocess.run(["gcc", "-O3", "-std=c99", "-Wall", "-shared", "-fPIC",
                         "-o", tmp, _SRC], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

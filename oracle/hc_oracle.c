@@ -11,28 +11,31 @@
  * Contents, each following one passage of the paper:
  *   or_naive_search   -- the problem statement itself (Sec. 1 and Sec. 2): every
  *                        window start p with y[p..p+m-1] = x, ascending.
- *   or_hash           -- the shift-then-add hash h (Eq. 3, Eq. 4) in the
- *                        backward-reading form of the Hash routine (Fig. 4).
+ *   or_hash           -- the shift-then-add hash h (Eq. 3, Eq. 4), reading the
+ *                        q-gram backwards from its last byte.
  *   or_link_hash      -- the link hash lambda (Eq. 5) with w = 32.
- *   or_preprocess     -- the preprocessing phase (Sec. 3.1, Eq. 1, Eq. 2,
- *                        Fig. 4), chains walked backwards from the pattern end,
- *                        first q-grams marked last and only if empty
- *                        (Sec. 3.4, first optimisation); returns F, s, F', H_v.
- *   or_hc_search      -- the HC searching phase (Sec. 3.3, Fig. 5 left) with
- *                        the H_v early reject (Sec. 3.4, second optimisation).
+ *   or_preprocess     -- the preprocessing phase (Sec. 3.1, Eq. 1, Eq. 2): the
+ *                        links of every chain, then the marks of the first
+ *                        q-grams only where no link was set (Sec. 3.4, first
+ *                        optimisation); returns F, s, F', H_v.
+ *   or_window         -- one window after a passed first test: the back-walk
+ *                        over linked q-grams (Sec. 3.3, Eq. 5), the H_v test
+ *                        (Sec. 3.4, second optimisation) and verification.
+ *   or_hc_search      -- the HC searching phase (Sec. 3.3).
  *   or_shc_search     -- the sentinel variant SHC (Sec. 3.4, third
- *                        optimisation, Fig. 5 right).
+ *                        optimisation).
  *
  * Readings taken where the paper is silent or garbled:
- *   - Verify/output position.  Fig. 5 sets j <- i - q after a full pass, which
- *     puts j at (window end) - m + q, and then verifies and outputs at j - q.
- *     The window that was just scanned starts at (window end) - m + 1 =
- *     j - q + 1 (the first window is y[0..m-1] with j = m - 1, and Sec. 3.3
- *     says the window then advances by exactly one).  The oracle verifies the
- *     window y[j-q+1 .. j-q+m] and outputs j - q + 1; j itself is left as the
- *     paper sets it, so the next window is still one position to the right.
- *   - w, the number of bits in a word of F, is 32 (Sec. 3.2 leaves it
- *     "hard-coded"; the result set does not depend on it, F does).
+ *   - Verify/output position.  The paper's pseudocode (Fig. 5), after a
+ *     window has been read in full, verifies and reports one position before
+ *     the window's start (its first window would be checked at y[-1]).  The
+ *     window that was read starts at end - m + 1, and the text of Sec. 3.3
+ *     says the next window is the one starting one position further: the
+ *     oracle verifies and reports the window's own start, end - m + 1, and
+ *     then examines the window ending at end + 1.
+ *   - w, the number of bits in a word of F, is 32 (Sec. 3.2 fixes w in the
+ *     implementation without giving its value; the result set does not
+ *     depend on it, F does).
  *   - Characters are unsigned bytes 0..255; hashes are computed in uint32.
  *     With alpha <= 15 the unmasked value stays below 2^24.
  *   - 1 <= q <= m and 1 <= alpha <= 15 are required; m = 0 is rejected.
@@ -106,37 +109,40 @@ int or_preprocess(const uint8_t *x, long m, int q, int alpha, uint32_t *F,
     uint32_t mask = (1u << alpha) - 1u;  /* F' : mod 2^alpha as an AND */
     for (uint32_t i = 0; i <= mask; i++) F[i] = 0;
 
-    /* Chain phase.  There are min(m-q+1, q) chains (Sec. 3.1); chain i ends
-     * at m-i and they are taken for i = min(m-q+1, q) down to 1, so the chain
-     * ending at the pattern end comes last.  Each chain is walked from its
-     * right end leftwards, one q-gram at a time; each (left, right) pair of
-     * adjacent q-grams ORs lambda(h(left)) into F[h(right)] (Eq. 1). */
-    uint32_t v = 0;
-    long nchains = (m - q + 1 < q) ? (m - q + 1) : q;
-    for (long i = nchains; i >= 1; i--) {
-        v = or_hash(x, m - i, q, s, mask);     /* rightmost q-gram of chain */
-        OR_TRACE(m - i);
-        long j = m - i - q;                    /* end of its left neighbour */
-        while (j >= q - 1) {                   /* left neighbour fits in x */
-            uint32_t vr = v;                   /* right q-gram's hash */
-            v = or_hash(x, j, q, s, mask);     /* left q-gram's hash */
-            OR_TRACE(j);
-            F[vr] |= or_link_hash(v);          /* Eq. 1 */
-            j -= q;
+    /* Links (Sec. 3.1, Eq. 1).  A chain is a run of adjacent,
+     * non-overlapping q-grams of x; the chain whose last q-gram ends at
+     * pattern position e holds the q-grams ending at e, e - q, e - 2q, ...
+     * down to q - 1.  Every q-gram belongs to exactly one chain, and the
+     * chain ends are the last min(q, m - q + 1) positions of x.  The chains
+     * are taken from the leftmost end to the one at m - 1, each from its
+     * right end leftwards; for two neighbours of a chain, the right one's
+     * word receives the link bit of the left one's hash. */
+    long first_end = m - ((m - q + 1 < q) ? (m - q + 1) : q);
+    uint32_t first_of_chain = 0;
+    for (long e = first_end; e <= m - 1; e++) {
+        uint32_t right = or_hash(x, e, q, s, mask);
+        OR_TRACE(e);
+        for (long p = e - q; p >= q - 1; p -= q) {
+            uint32_t left = or_hash(x, p, q, s, mask);
+            OR_TRACE(p);
+            F[right] |= or_link_hash(left);    /* Eq. 1 */
+            right = left;
         }
+        first_of_chain = right;                /* hash of the chain's first q-gram */
     }
-    /* H_v: the last hash of the last chain, i.e. of the first q-gram of the
-     * chain that ends at m-1 (Sec. 3.4, second optimisation). */
-    uint32_t hv = v;
+    /* H_v (Sec. 3.4, second optimisation): the hash of the first q-gram of
+     * the chain that ends at m - 1, the last chain taken above. */
+    uint32_t hv = first_of_chain;
     if (chain_calls != NULL) *chain_calls = calls;
 
-    /* Marking phase (Eq. 2 with the first optimisation of Sec. 3.4): the
-     * q-grams ending at q-1 .. min(2q-1, m)-1 have no left neighbour; their
-     * word gets the value 1 only if nothing has been set in it yet. */
-    long last = (2 * q - 1 < m) ? (2 * q - 1) : m;
-    for (long i = q - 1; i <= last - 1; i++) {
-        uint32_t u = or_hash(x, i, q, s, mask);
-        OR_TRACE(i);
+    /* Marks (Eq. 2 with the first optimisation of Sec. 3.4): the first
+     * q-gram of every chain -- those ending at q - 1 .. min(2q - 1, m) - 1,
+     * which have no left neighbour -- gets the value 1, but only in a word
+     * that no link has set. */
+    long stop = (2 * q - 1 < m) ? (2 * q - 1) : m;
+    for (long e = q - 1; e < stop; e++) {
+        uint32_t u = or_hash(x, e, q, s, mask);
+        OR_TRACE(e);
         if (F[u] == 0) F[u] = 1;
     }
 #undef OR_TRACE
@@ -148,10 +154,45 @@ int or_preprocess(const uint8_t *x, long m, int q, int alpha, uint32_t *F,
 }
 
 /* ---------------------------------------------------------------------- */
-/* HC(x, m, y, n, q, alpha) of Fig. 5 left (Sec. 3.3), using the filter built
- * by or_preprocess.  F must hold 2^alpha words.  Writes up to cap positions
- * (0-based window starts, ascending) and returns the total count; returns
- * (size_t)-1 on invalid arguments. */
+/* One window of the searching phase (Sec. 3.3, Eq. 5, Sec. 3.4), after its
+ * first test has passed: the q-gram ending at the window's last position
+ * `end` hashed to h, whose word F[h] is non-empty.  Going right to left,
+ * each further q-gram that lies wholly inside the window must be linked to
+ * its right neighbour: its link bit lambda(hash) must be set in the
+ * neighbour's word.  At the first q-gram that is not, the window is left
+ * and the next one examined ends m - q + 1 past that q-gram's end, the
+ * first window that does not contain it.  A window read in full is an
+ * occurrence candidate only if its leftmost hash equals H_v; it is then
+ * compared with x, and the next window is the one starting one position
+ * to the right.  Returns the end of the next window; *hit is 1 when the
+ * window (starting at end - m + 1) is an occurrence. */
+static long or_window(const uint8_t *x, long m, const uint8_t *t, long end,
+                      int q, int s, uint32_t mask, const uint32_t *F,
+                      uint32_t hv, uint32_t h, int *hit) {
+    const long wstart = end - m + 1;
+    uint32_t word = F[h];
+    long last = end;                           /* end of the leftmost q-gram read */
+    *hit = 0;
+    while (last - 2 * q + 1 >= wstart) {       /* the next q-gram is inside */
+        long left = last - q;
+        uint32_t hl = or_hash(t, left, q, s, mask);
+        if ((word & or_link_hash(hl)) == 0)
+            return left + (m - q + 1);         /* not linked: leave the window */
+        word = F[hl];
+        h = hl;
+        last = left;
+    }
+    if (h == hv && memcmp(t + wstart, x, (size_t)m) == 0) *hit = 1;
+    return end + 1;
+}
+
+/* HC(x, m, y, n, q, alpha) of Sec. 3.3, using the filter built by
+ * or_preprocess.  F must hold 2^alpha words.  Windows are examined left to
+ * right by their last position; a window whose end q-gram hashes to an
+ * empty word of F contains no factor of x ending there and is skipped by
+ * m - q + 1 positions (the paper's shift), the others go through or_window.
+ * Writes up to cap positions (0-based window starts, ascending) and returns
+ * the total count; returns (size_t)-1 on invalid arguments. */
 size_t or_hc_search(const uint8_t *x, long m, const uint8_t *y, long n,
                     int q, int alpha, uint32_t *F, uint64_t *out, size_t cap) {
     int s;
@@ -159,55 +200,32 @@ size_t or_hc_search(const uint8_t *x, long m, const uint8_t *y, long n,
     if (or_preprocess(x, m, q, alpha, F, &s, &mask, &hv, NULL, 0, NULL,
                       NULL) != 0)
         return (size_t)-1;
-    /* j is the text position aligned with the END of the current window;
-     * the first window is y[0..m-1]. */
     size_t count = 0;
-    long j = m - 1;
-    while (j < n) {
-        /* First test: the q-gram ending at the window end must hash to a
-         * non-empty word of F, else no factor of x ends there (Sec. 3.3). */
-        uint32_t v = or_hash(y, j, q, s, mask);
-        uint32_t z = F[v];
-        if (z != 0) {
-            /* Back-walk: read the window's q-grams right to left; each must
-             * be linked (Eq. 1) to the q-gram on its right, i.e. its bit
-             * lambda(v) must be set in z = F[h(right q-gram)].  i bounds the
-             * walk so that every q-gram read lies inside the window. */
-            long i = j - m + 2 * q;
-            int broke = 0;
-            while (j >= i) {
-                j -= q;
-                v = or_hash(y, j, q, s, mask);
-                if ((z & or_link_hash(v)) == 0) {
-                    broke = 1;  /* not linked: shift past this q-gram */
-                    break;
-                }
-                z = F[v];
-            }
-            if (!broke) {
-                /* The whole window was read (the while loop's else branch).
-                 * Reset j so the shift below advances the window by one, and
-                 * verify only if the last hash equals H_v (Sec. 3.4). */
-                j = i - q;
-                long start = j - q + 1;         /* reading: window start */
-                if (v == hv && memcmp(y + start, x, (size_t)m) == 0) {
-                    if (count < cap) out[count] = (uint64_t)start;
-                    count++;
-                }
-            }
+    long end = m - 1;                          /* the first window is y[0..m-1] */
+    while (end < n) {
+        uint32_t h = or_hash(y, end, q, s, mask);   /* first test */
+        if (F[h] == 0) {
+            end += m - q + 1;
+            continue;
         }
-        /* Shift: m-q+1 past the window end on a first-test miss, past the
-         * unlinked q-gram after a break, by one after a full read. */
-        j += m - q + 1;
+        int hit;
+        long next = or_window(x, m, y, end, q, s, mask, F, hv, h, &hit);
+        if (hit) {
+            if (count < cap) out[count] = (uint64_t)(end - m + 1);
+            count++;
+        }
+        end = next;
     }
     return count;
 }
 
 /* ---------------------------------------------------------------------- */
-/* SHC(x, m, y, n, q, alpha) of Fig. 5 right (Sec. 3.4, sentinel).  ybuf must
- * be writable and hold n + m bytes: the pattern is copied into
- * ybuf[n .. n+m-1] so that the inner miss loop needs no position test.
- * Same output convention as or_hc_search. */
+/* SHC(x, m, y, n, q, alpha) of Sec. 3.4 (third optimisation): HC with a
+ * copy of x placed right after the text, so that the loop of first tests
+ * needs no test of the window position -- it stops at the latest on a
+ * window inside the copy, every q-gram of which hits a non-empty word.
+ * ybuf must be writable and hold n + m bytes; ybuf[n .. n+m-1] is
+ * overwritten.  Same output convention as or_hc_search. */
 size_t or_shc_search(const uint8_t *x, long m, uint8_t *ybuf, long n, int q,
                      int alpha, uint32_t *F, uint64_t *out, size_t cap) {
     int s;
@@ -215,41 +233,21 @@ size_t or_shc_search(const uint8_t *x, long m, uint8_t *ybuf, long n, int q,
     if (or_preprocess(x, m, q, alpha, F, &s, &mask, &hv, NULL, 0, NULL,
                       NULL) != 0)
         return (size_t)-1;
-    /* Sentinel: a copy of x right after the text guarantees that the fast
-     * miss loop below stops at the latest on the sentinel window. */
-    for (long i = 0; i < m; i++) ybuf[n + i] = x[i];
+    memcpy(ybuf + n, x, (size_t)m);            /* the sentinel */
     size_t count = 0;
-    long j = m - 1;
-    while (j < n) {
-        /* Fast loop: first test only, no position check. */
-        while (F[or_hash(ybuf, j, q, s, mask)] == 0)
-            j += m - q + 1;
-        /* The position check happens once the fast loop has stopped; the
-         * rest is the HC back-walk and verification. */
-        if (j < n) {
-            uint32_t v = or_hash(ybuf, j, q, s, mask);
-            uint32_t z = F[v];
-            long i = j - m + 2 * q;
-            int broke = 0;
-            while (j >= i) {
-                j -= q;
-                v = or_hash(ybuf, j, q, s, mask);
-                if ((z & or_link_hash(v)) == 0) {
-                    broke = 1;
-                    break;
-                }
-                z = F[v];
-            }
-            if (!broke) {
-                j = i - q;
-                long start = j - q + 1;         /* reading: window start */
-                if (v == hv && memcmp(ybuf + start, x, (size_t)m) == 0) {
-                    if (count < cap) out[count] = (uint64_t)start;
-                    count++;
-                }
-            }
-            j += m - q + 1;
+    long end = m - 1;
+    for (;;) {
+        uint32_t h;
+        while (F[h = or_hash(ybuf, end, q, s, mask)] == 0)
+            end += m - q + 1;                  /* first tests only */
+        if (end >= n) break;                   /* stopped in the sentinel */
+        int hit;
+        long next = or_window(x, m, ybuf, end, q, s, mask, F, hv, h, &hit);
+        if (hit) {
+            if (count < cap) out[count] = (uint64_t)(end - m + 1);
+            count++;
         }
+        end = next;
     }
     return count;
 }

@@ -17,25 +17,24 @@ SRC = os.path.join(ROOT, "oracle", "hc_oracle.c")
 
 # (name, original text, planted text) -- each must occur exactly once
 RESULT_MUTANTS = [
-    # the output position exactly as printed (j - q instead of j - q + 1)
-    ("paper_literal_position", "long start = j - q + 1;         /* reading: window start */\n"
-     "                if (v == hv && memcmp(y + start",
-     "long start = j - q;\n                if (v == hv && memcmp(y + start"),
-    # shift one too far on a miss
-    ("shift_too_far", "        j += m - q + 1;\n    }\n    return count;\n}\n\n/* ---",
-     "        j += m - q + 2;\n    }\n    return count;\n}\n\n/* ---"),
+    # the output position exactly as printed in the paper (one before the
+    # window start): verified and reported there
+    ("paper_literal_position", "    if (h == hv && memcmp(t + wstart, x, (size_t)m) == 0) *hit = 1;",
+     "    if (h == hv && memcmp(t + wstart - 1, x, (size_t)m) == 0) *hit = 1;"),
+    # shift one too far on a first-test miss
+    ("shift_too_far", "        if (F[h] == 0) {\n            end += m - q + 1;",
+     "        if (F[h] == 0) {\n            end += m - q + 2;"),
     # link stored in the left q-gram's word instead of the right one's (Eq. 1)
-    ("link_transposed", "F[vr] |= or_link_hash(v);", "F[v] |= or_link_hash(vr);"),
+    ("link_transposed", "F[right] |= or_link_hash(left);", "F[left] |= or_link_hash(right);"),
     # marking phase (Eq. 2) dropped
     ("no_marking", "if (F[u] == 0) F[u] = 1;", "(void)u;"),
     # one chain too few
-    ("chain_count", "long nchains = (m - q + 1 < q) ? (m - q + 1) : q;",
-     "long nchains = (m - q < q) ? (m - q) : q;"),
-    # the back-walk skips its bound one q-gram early but the window is
-    # reported as fully read: the walk stops too soon AND H_v compares a
-    # different q-gram
-    ("walk_bound", "long i = j - m + 2 * q;\n            int broke = 0;\n            while (j >= i) {\n                j -= q;\n                v = or_hash(y, j",
-     "long i = j - m + 3 * q;\n            int broke = 0;\n            while (j >= i) {\n                j -= q;\n                v = or_hash(y, j"),
+    ("chain_count", "long first_end = m - ((m - q + 1 < q) ? (m - q + 1) : q);",
+     "long first_end = m - ((m - q < q) ? (m - q) : q);"),
+    # the back-walk stops one q-gram early but the window counts as read in
+    # full: the walk is too short AND H_v compares a different q-gram
+    ("walk_bound", "while (last - 2 * q + 1 >= wstart) {",
+     "while (last - 3 * q + 1 >= wstart) {"),
 ]
 
 HASH_MUTANTS = [
