@@ -257,19 +257,19 @@ def dense_single_pass(opts, m: int) -> bool:
     """Whether the library runs a dense (m = q) search as its single-pass
     kernel: the same rule as its planner (chunks of 256 * L window starts,
     L even, tiles of at most 64 steps of 512 windows, staging buffers and
-    step masks within the 227 KB of shared memory per block)."""
-    if opts is not None and getattr(opts, "single_pass", 0) < 0:
+    two tiles' step masks within the 227 KB of shared memory per block)."""
+    if opts is None or getattr(opts, "single_pass", 0) != 1:
         return False
     lane = opts.lane_bytes if opts is not None and opts.lane_bytes else 8
     stages = opts.stages if opts is not None and opts.stages else 2
     ls = max(2, (lane + 1) & ~1)
     spc = ls // 2
-    want = opts.tile_steps if opts is not None and getattr(opts, "tile_steps", 0) else 32
+    want = opts.tile_steps if opts is not None and getattr(opts, "tile_steps", 0) else 16
     tc = max(1, -(-want // spc))
     if spc * tc > 64:
         return False
     stage = ((16 + 256 * ls + m - 1 + 15) & ~15) + 32
-    return 8 * stages * stage + 8 * spc * tc * 64 + 1024 <= 227 * 1024
+    return 8 * stages * stage + 8 * 2 * spc * tc * 64 + 1024 <= 227 * 1024
 
 
 KERNEL_SOURCES = ("paper_2310_15711_gb300/csrc/hc_kernels.cuh", "paper_2310_15711_gb300/csrc/hc_search.cu",

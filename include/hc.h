@@ -107,9 +107,10 @@ int hc_filter_to_device(hc_filter *f);
  * element of a uint64 array is), else HC_ERR_ARG.  Nothing is waited for.  The first call
  * with a filter copies it to the device (see hc_filter_to_device).  Each call
  * takes a stream-ordered workspace from the library's memory pool and gives
- * it back after its kernels: 16 bytes per CTA plus 4 bytes per spilled
- * position (by default min(n-m+1, max(cap, 2^20)) of them); the pool keeps
- * freed memory for reuse.  n < m is not an error: the count is 0.  Errors:
+ * it back after its kernels: 16 bytes per warp plus 4 bytes per spilled
+ * position (by default min(n-m+1, max(cap, 2^20)) of them), or for the
+ * single-pass dense form (m = q) 8 bytes per tile of 8192 window starts;
+ * the pool keeps freed memory for reuse.  n < m is not an error: the count is 0.  Errors:
  * HC_ERR_ARG, HC_ERR_CUDA, HC_ERR_NOMEM; a device wait that gave up is
  * reported by the next hc_search/hc_check_status.
  */
@@ -153,12 +154,17 @@ typedef struct hc_search_opts {
     int pos32;              /* 1: positions written as uint32 (pos_dev holds cap
                                uint32 values, 4-byte aligned; needs
                                n - m + 1 <= 2^32); 0: uint64 */
-    int single_pass;        /* dense mode: 0 or 1 -- one kernel writes the
+    int single_pass;        /* dense mode: 1 -- one kernel writes the
                                positions in text order as it goes (tiles
-                               claimed in order, counts of earlier tiles by a
-                               look-back), after a small kernel that zeroes
-                               its tile table; -1 -- spill regions and a
-                               second kernel (emit) */
+                               claimed in order; a tile's output offset is
+                               the sum of the counts of the tiles before it,
+                               read from per-tile entries and a tree of group
+                               totals), after a small kernel that zeroes
+                               those counts; 0 or -1 -- the positions are
+                               held in spill regions and a second kernel
+                               (emit) writes them (the automatic choice: a
+                               tile of the single pass waits for the slowest
+                               earlier tile, which measured slower on GB300) */
     int tile_steps;         /* single pass: window steps of 512 per tile
                                (1..64, rounded up to whole chunks);
                                0 = automatic */
@@ -373,6 +379,11 @@ typedef struct hc_server_config {
     int batch_only;         /* 1: every request runs the batched kernels (0:
                                a lone request, and m = q requests in batches
                                of <= 16, run the single-search kernels) */
+    uint64_t max_batch_bytes; /* text bytes per batch (a single larger request
+                               still runs, alone); a backlog is cut into
+                               batches of at most this much text that run on
+                               several streams and complete one by one;
+                               0 = 64 MiB */
 } hc_server_config;
 
 typedef struct hc_server_request {
@@ -516,7 +527,8 @@ uint64_t hc_kernel_launches(void);
  * (ms[k]) and launch counts (launches[k]); either array may be NULL.  With
  * reset != 0 the recorded launches are then forgotten.  Families:
  * hc_timing_kind_name(k) for k = 0.. ("scan_staged", "scan_direct",
- * "scan_dense", "emit", "preprocess", "batch"; "" past the last).  Errors:
+ * "scan_dense", "emit", "preprocess", "batch", "lb_init" -- the kernel that
+ * zeroes a single-pass search's tile table; "" past the last).  Errors:
  * HC_ERR_CUDA. */
 int hc_timing_enable(int on);
 int hc_timing_report(double *ms, uint64_t *launches, int nkinds, int reset);

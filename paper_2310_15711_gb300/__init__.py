@@ -568,12 +568,12 @@ class ServerConfig(ctypes.Structure):
     """hc_server_config (zero = default)."""
     _fields_ = [("struct_size", _sz), ("mem_limit", ctypes.c_uint64), ("max_inflight", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("default_cap", ctypes.c_uint64), ("plain", ctypes.c_int),
-                ("batch_only", ctypes.c_int)]
+                ("batch_only", ctypes.c_int), ("max_batch_bytes", ctypes.c_uint64)]
 
     def __init__(self, mem_limit=0, max_inflight=0, max_batch=0, default_cap=0, plain=0,
-                 batch_only=0):
+                 batch_only=0, max_batch_bytes=0):
         super().__init__(ctypes.sizeof(ServerConfig), mem_limit, max_inflight, max_batch, default_cap,
-                         plain, batch_only)
+                         plain, batch_only, max_batch_bytes)
 
 
 class ServerRequest(ctypes.Structure):

@@ -9,20 +9,26 @@
 //
 // Output in text order in one pass.  The window starts are cut into chunks
 // of C starts (the bulk-copy unit) and tiles of tile_chunks consecutive
-// chunks (the ordering unit).  A warp claims tiles from an atomic ticket, so
-// tiles are claimed in text order by running warps; it streams each tile's
+// chunks (the ordering unit).  Warps claim tiles from atomic counters, in
+// about text order, by running warps; a warp streams each tile's
 // chunks through its own ring of shared-memory buffers (1-D bulk copies on
 // mbarriers) and keeps one 16-bit match mask per lane and 512-window step in
-// shared memory.  At the end of a tile it publishes the tile's match count
-// in the tile's descriptor, sums the counts of the tiles before it by a
-// decoupled look-back (32 descriptors per read, stopping at the first tile
-// whose inclusive count is known), publishes its own inclusive count and
+// shared memory.  At the end of a tile it adds the tile's match count to the
+// nodes of a Fenwick tree over the tiles (each node also counts the tiles
+// added to it), reads the popcount(t) nodes that together cover tiles 0..t-1
+// -- one round of loads, waiting only until those nodes are complete -- and
 // writes its positions straight to the output.  A tile only waits for tiles
-// claimed before it, whose warps are running, so the waits always end; every
-// wait is bounded all the same (a wait that gives up sets the status flag).
-// The last tile writes the total count.  An init kernel, launched before the
-// scan, zeroes the ticket and the descriptors; the scan is its programmatic
+// claimed before it, whose warps are running, so the waits end; every wait
+// is bounded all the same (a wait that gives up sets the status flag).  The
+// last tile writes the total count.  An init kernel, launched before the
+// scan, zeroes the ticket and the tree; the scan is its programmatic
 // dependent and waits for it before claiming a tile.
+//
+// (A chain of per-tile descriptors -- the usual decoupled look-back -- was
+// measured first: when thousands of warps finish their tiles at about the
+// same time, the inclusive counts travel along the chain a few hundred
+// tiles per read, which made the scan up to twice as slow; the tree needs
+// one read of at most log2(T) nodes.)
 #include <cstdint>
 
 #include "hc_device.cuh"
@@ -33,67 +39,30 @@ namespace hc {
 
 namespace {
 
-// Tile descriptor: state in bits 62-63, count in bits 0-61.
-constexpr unsigned long long kDescAggregate = 1ull << 62;  // the tile's own count
-constexpr unsigned long long kDescInclusive = 2ull << 62;  // count of tiles 0..t
-constexpr unsigned long long kDescCount = (1ull << 62) - 1;
+// Tile counters (see claim() in the scan): one per warp of a CTA.
+constexpr int kTicketCounters = kWarps;
+// Tiles per group (the group's total is one hot counter of this many adds).
+constexpr unsigned int kGroupTiles = static_cast<unsigned int>(kSinglePassGroup);
 
-// Zeroes the ticket and the tile descriptors of one single-pass search.
+// Counts of the tiles: tile t's entry holds its match count (bits 0-30,
+// at most 32768 windows per tile) and a ready bit (31); a group's total and
+// a node of the group tree hold the tiles (groups) added in bits 40-63 and
+// their matches in bits 0-39.
+constexpr unsigned int kTileReady = 1u << 31;
+constexpr int kAddedShift = 40;
+constexpr unsigned long long kOneAdded = 1ull << kAddedShift;
+constexpr unsigned long long kCountBits = kOneAdded - 1;
+
+// Zeroes the tile counters, the tile entries, the group totals and the
+// group tree of one single-pass search.
 __global__ void __launch_bounds__(kThreads) hc_single_pass_init_kernel(const SearchArgs a) {
   pdl_launch_dependents();  // the scan may be scheduled; it waits for this grid
   const unsigned long long i0 = static_cast<unsigned long long>(blockIdx.x) * kThreads + threadIdx.x;
   const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * kThreads;
-  if (i0 == 0) *a.lb_ticket = 0u;
-  for (unsigned long long i = i0; i < a.num_tiles; i += stride) a.lb_desc[i] = 0ull;
-}
-
-// Bytes at lane-relative offset off .. off+3 of the 24 bytes Tw holds.
-template <int OFF>
-__device__ __forceinline__ uint32_t text_word(const uint32_t (&Tw)[6]) {
-  if constexpr ((OFF & 3) == 0) return Tw[OFF >> 2];
-  else return __funnelshift_r(Tw[OFF >> 2], Tw[(OFF >> 2) + 1], 8u * (OFF & 3));
-}
-
-// Column set of the byte test: 0 = every column c < Q; 1 = the first
-// stage of the two-stage test (columns 0, 1, 4, 5: the cheapest four, two
-// of them word-aligned); 2 = the remaining columns.
-template <int SET>
-__device__ __forceinline__ constexpr bool in_set(int c) {
-  return SET == 0 || ((SET == 1) == ((c & 2) == 0));
-}
-
-// d[g] |= OR over the columns c of SET of (text bytes at 4g + c) ^ x[c]
-// replicated: byte k of d[g] stays 0 while window 4g + k agrees with x on
-// those columns.
-template <int Q, int SET, int G, int C>
-__device__ __forceinline__ void or_columns(const uint32_t (&Tw)[6], const uint32_t (&xrep)[Q],
-                                           uint32_t (&d)[4]) {
-  if constexpr (C < Q) {
-    if constexpr (in_set<SET>(C)) d[G] |= text_word<4 * G + C>(Tw) ^ xrep[C];
-    or_columns<Q, SET, G, C + 1>(Tw, xrep, d);
-  } else if constexpr (G < 3) {
-    or_columns<Q, SET, G + 1, 0>(Tw, xrep, d);
-  }
-}
-
-// Bit 7 of byte k of the result is set iff byte k of d is zero (exact for
-// every byte).
-__device__ __forceinline__ uint32_t zero_bytes(uint32_t d) {
-  return ~(((d & 0x7f7f7f7fu) + 0x7f7f7f7fu) | d | 0x7f7f7f7fu);
-}
-
-// Nonzero iff d has a zero byte (the lowest zero byte is always flagged;
-// bytes above it may be flagged wrongly, so only the test is used).
-__device__ __forceinline__ uint32_t has_zero_byte(uint32_t d) {
-  return (d - 0x01010101u) & ~d & 0x80808080u;
-}
-
-// 16-bit mask, bit 4g + k set iff bit 8k + 7 of z[g] is set.
-__device__ __forceinline__ uint32_t gather_mask(const uint32_t (&z)[4]) {
-  uint32_t m = 0;
-#pragma unroll
-  for (int g = 0; g < 4; ++g) m |= (((z[g] >> 7) * 0x01020408u) >> 24) << (4 * g);
-  return m;
+  if (i0 < kTicketCounters) a.lb_ticket[i0] = 0u;
+  for (unsigned long long i = i0; i < a.num_tiles; i += stride) a.lb_desc[i] = 0u;
+  for (unsigned long long i = i0; i < a.num_groups; i += stride) a.lb_gpack[i] = 0ull;
+  for (unsigned long long i = i0; i <= a.num_groups; i += stride) a.lb_gtree[i] = 0ull;
 }
 
 }  // namespace
@@ -101,9 +70,9 @@ __device__ __forceinline__ uint32_t gather_mask(const uint32_t (&z)[4]) {
 // ---------------------------------------------------------------------------
 // The scan.  Warp-level worker: lane 0 claims tiles and drives the bulk
 // copies; the warp tests 512 windows per step (16 per lane).  Shared
-// memory per warp: `stages` staging buffers, then flag_steps * 32 masks.
+// memory per warp: `stages` staging buffers, then 2 * flag_steps * 32 masks.
 template <int Q>
-__global__ void __launch_bounds__(kThreads) hc_dense_single_pass_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) hc_dense_single_pass_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
   __shared__ long long s_chunk[kWarps][kMaxStages];  // chunk in each buffer, -1: none
@@ -116,7 +85,7 @@ __global__ void __launch_bounds__(kThreads) hc_dense_single_pass_kernel(const Se
   const int head = a.head;
   uint8_t* stages = smem + static_cast<size_t>(warp) * nst * a.stage_bytes;
   uint16_t* flags = reinterpret_cast<uint16_t*>(smem + static_cast<size_t>(kWarps) * nst * a.stage_bytes) +
-                    static_cast<size_t>(warp) * a.flag_steps * 32;
+                    static_cast<size_t>(warp) * 2 * a.flag_steps * 32;
   uint64_t* wb = bars[warp];
   long long* my_chunk = s_chunk[warp];
 
@@ -140,27 +109,43 @@ __global__ void __launch_bounds__(kThreads) hc_dense_single_pass_kernel(const Se
   __syncwarp();
   pdl_wait();  // the init kernel has zeroed the ticket and the descriptors
 
-  // Lane 0's claim state: tile being staged (cur_t, chunk cur_k of cur_nk)
-  // and the next tile, claimed one tile ahead so that the atomic's latency
-  // is hidden.  A warp processes its tiles in the order it claims them.
-  long long cur_t = -1, res_t = -1;
+  // Lane 0's claim state: the tile being staged (cur_t, its chunk cur_k of
+  // cur_nk) and the next one, claimed when the last chunk of the current
+  // tile is staged and first used at the next staging, so the atomic's
+  // latency overlaps the scan of a chunk.  Every tile is thus claimed about
+  // the same time (the ring's depth plus one chunk) before its scan begins,
+  // and tiles are scanned in about the order they are claimed: a tile's
+  // look-back seldom waits for a tile claimed long before it.
+  int cur_t = -1, next_t = -1;
   int cur_k = 0, cur_nk = 0;
   const long long num_tiles = static_cast<long long>(a.num_tiles);
   const long long num_chunks = static_cast<long long>(a.num_chunks);
   auto tile_chunks = [&](long long t) { return static_cast<int>(min(static_cast<long long>(TC), num_chunks - t * TC)); };
+  // Tiles are handed out by kTicketCounters counters, counter j (the warp's
+  // index in its CTA) giving tiles j, j + kTicketCounters, ... in order:
+  // each counter sees a few atomics per microsecond, where one counter for
+  // the whole grid made the claims queue (the latency of an atomic on one
+  // hot address grows with the rate).  A tile still waits only for lower
+  // tiles, each of which is claimed, or will be claimed, by a warp that is
+  // not waiting for a higher tile.
+  auto claim = [&]() -> int {
+    const unsigned int r = atomicAdd(a.lb_ticket + warp, 1u);
+    return static_cast<int>(min(r * kTicketCounters + warp, 0x7fffffffu));
+  };
   auto next_chunk = [&]() -> long long {
     if (cur_t < 0) return -1;
     if (cur_k == cur_nk) {
-      cur_t = res_t;
+      cur_t = next_t;
       if (cur_t >= num_tiles) {
         cur_t = -1;
         return -1;
       }
       cur_k = 0;
       cur_nk = tile_chunks(cur_t);
-      res_t = static_cast<long long>(atomicAdd(a.lb_ticket, 1u));
     }
-    return cur_t * TC + cur_k++;
+    const long long c = static_cast<long long>(cur_t) * TC + cur_k++;
+    if (cur_k == cur_nk) next_t = claim();
+    return c;
   };
   // stages chunk c (window starts [cC - head, cC - head + C)) in buffer st;
   // the copy starts at the 16-byte aligned text address y - head + cC
@@ -175,21 +160,151 @@ __global__ void __launch_bounds__(kThreads) hc_dense_single_pass_kernel(const Se
     bulk_copy_g2s(stages + static_cast<size_t>(st) * a.stage_bytes, a.y - head + cs, bytes, &wb[st]);
   };
   if (lane == 0) {
-    cur_t = static_cast<long long>(atomicAdd(a.lb_ticket, 1u));
-    res_t = static_cast<long long>(atomicAdd(a.lb_ticket, 1u));
+    cur_t = claim();
     if (cur_t >= num_tiles) cur_t = -1;
     else cur_nk = tile_chunks(cur_t);
     for (int k = 0; k < nst; ++k) issue(k, next_chunk());
   }
   __syncwarp();
 
-  uint32_t lane_cnt = 0;      // matches of this lane in the current tile
+  uint32_t lane_cnt = 0;            // matches of this lane in the current tile
   unsigned long long stepbits = 0;  // steps of the current tile with a match
-  int single_left = 0;        // chunks left in the one-stage byte test (Q >= 5)
+  int single_left = 0;              // chunks left in the one-stage byte test (Q >= 5)
   bool ok = true;
-  bool refilled = false;  // a failed look-back left buffer st refilled
+  bool refilled = false;            // a wait gave up after buffer st was refilled
   int st = 0;
   uint32_t phase = 0;
+  int fb = 0;                       // flag buffer of the current tile (two per warp)
+  const int fstride = a.flag_steps * 32;
+  // The pending tile: scanned, its count added to the tree, its positions
+  // not yet written.  Its prefix is read without waiting while the next
+  // tile is scanned, and its positions are written as soon as the prefix is
+  // complete -- at the latest when the next tile is scanned, before that
+  // tile's buffer is needed again.
+  int p_t = -1;                     // its index (-1: none)
+  int p_fb = 0;
+  unsigned long long p_bits = 0, p_agg = 0;
+  // this lane's part of the pending tile's prefix: the entries of tiles
+  // base + lane and base + 32 + lane of its group (those below it), and one
+  // node of the group tree
+  unsigned int p_va = 0, p_vb = 0, p_node = 0;
+  unsigned long long p_vc = 0;
+  bool p_ha = false, p_hb = false, p_hc = false;
+  // lane 0: the group total returned by the last tile's atomic add, to be
+  // examined (its latency overlaps a chunk's scan): if that tile completed
+  // its group, the group goes into the group tree
+  bool g_pending = false;
+  unsigned long long g_old = 0, g_agg = 0;
+  unsigned int g_idx = 0, g_size = 0;
+
+  // Writes the positions of tile pt (masks in flag buffer pfb, steps pbits),
+  // after `excl` earlier occurrences, in text order: steps, lanes, windows.
+  auto write_tile = [&](long long pt, int pfb, unsigned long long pbits, unsigned long long excl) {
+    const uint16_t* fl = flags + pfb * fstride;
+    const long long tile_w0 = pt * TC * static_cast<long long>(C) - head;
+    unsigned long long run = excl;
+    for (unsigned long long sbits = pbits; sbits; sbits &= sbits - 1) {
+      const int s = __ffsll(static_cast<long long>(sbits)) - 1;
+      uint32_t m16 = HC_IN_BOUNDS(s < a.flag_steps) ? fl[s * 32 + lane] : 0u;
+      const uint32_t mine = static_cast<uint32_t>(__popc(m16));
+      const uint32_t incl = warp_incl_scan_u32(mine);
+      unsigned long long o = run + (incl - mine);
+      const unsigned long long pbase =
+          static_cast<unsigned long long>(tile_w0 + (static_cast<long long>(s) << 9) + 16 * lane);
+      for (; m16; m16 &= m16 - 1u, ++o) {
+        if (o >= a.cap) break;
+        const unsigned long long pos = pbase + static_cast<unsigned>(__ffs(m16) - 1);
+        if (a.pos32) reinterpret_cast<uint32_t*>(a.pos)[o] = static_cast<uint32_t>(pos);
+        else a.pos[o] = pos;
+      }
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  };
+  // The occurrences before tile t (group g = t / kGroupTiles) are those of
+  // the groups before g -- the group-tree nodes g, g - lowbit(g), ..., one
+  // per set bit of g, complete when all lowbit(node) groups have been added
+  // -- plus those of the tiles of group g below t, each ready once its entry
+  // is written.  All of them were claimed before t by running warps, so a
+  // wait for them ends.  Lane k reads the k-th node and two tile entries:
+  // one round of loads.
+  auto start_prefix = [&](long long t) {
+    const unsigned int ut = static_cast<unsigned int>(t);
+    const unsigned int g = ut / kGroupTiles, base = g * kGroupTiles;
+    const int nt = static_cast<int>(ut - base);
+    const int nodes = __popc(g);
+    unsigned int node = g;
+    for (int k = 0; k < lane && k < nodes; ++k) node &= node - 1;
+    p_ha = lane < nt;
+    p_hb = lane + 32 < nt;
+    p_hc = lane < nodes;
+    p_node = node;
+    p_va = p_ha ? ld_relaxed_u32(a.lb_desc + base + lane) : 0u;
+    p_vb = p_hb ? ld_relaxed_u32(a.lb_desc + base + 32 + lane) : 0u;
+    p_vc = p_hc ? ld_relaxed_u64(a.lb_gtree + node) : 0ull;
+  };
+  auto lane_complete = [&]() -> bool {
+    return (!p_ha || (p_va & kTileReady)) && (!p_hb || (p_vb & kTileReady)) &&
+           (!p_hc || (p_vc >> kAddedShift) == (p_node & (0u - p_node)));
+  };
+  auto reload = [&]() {
+    const unsigned int base = static_cast<unsigned int>(p_t) / kGroupTiles * kGroupTiles;
+    if (p_ha && !(p_va & kTileReady)) p_va = ld_relaxed_u32(a.lb_desc + base + lane);
+    if (p_hb && !(p_vb & kTileReady)) p_vb = ld_relaxed_u32(a.lb_desc + base + 32 + lane);
+    if (p_hc && (p_vc >> kAddedShift) != (p_node & (0u - p_node))) p_vc = ld_relaxed_u64(a.lb_gtree + p_node);
+  };
+  // true when the pending tile's prefix is complete; else the incomplete
+  // parts are loaded again (no waiting)
+  auto prefix_ready = [&]() -> bool {
+    const bool complete = lane_complete();
+    if (__all_sync(0xffffffffu, complete)) return true;
+    if (!complete) reload();
+    return false;
+  };
+  // lane 0: adds a group completed by this warp's last tile to the group
+  // tree (nodes g+1, g+1+lowbit, ... <= number of groups)
+  auto push_group = [&]() {
+    if (lane == 0 && g_pending) {
+      g_pending = false;
+      if ((g_old >> kAddedShift) + 1 == g_size) {
+        const unsigned long long add = kOneAdded | ((g_old & kCountBits) + g_agg);
+        for (unsigned int i = g_idx + 1; i <= static_cast<unsigned int>(a.num_groups); i += i & (0u - i))
+          atomicAdd(a.lb_gtree + i, add);
+      }
+    }
+  };
+  // waits until the pending tile's prefix is complete (bounded, a short
+  // sleep between reads; given up at once if another wait already gave up);
+  // false if the wait gave up
+  auto wait_prefix = [&]() -> bool {
+    push_group();  // a warp never waits while a group it completed is not in the tree
+    bool complete = lane_complete();
+    if (__all_sync(0xffffffffu, complete)) return true;
+    const uint64_t t0 = global_timer_ns();
+    bool give_up = false;
+    for (uint32_t spins = 1; !complete && !give_up; ++spins) {
+      __nanosleep(64);
+      reload();
+      complete = lane_complete();
+      if (!complete && (spins & 15u) == 0u)
+        give_up = global_timer_ns() - t0 > kWaitLimitNs || spins >= kMaxSpins ||
+                  (ld_relaxed_u32(a.status) & 1u) != 0u;
+    }
+    if (__any_sync(0xffffffffu, give_up)) {
+      if (lane == 0) atomicOr(a.status, 1u);
+      return false;
+    }
+    return true;
+  };
+  // writes the pending tile (its prefix complete) and the total after the
+  // last tile
+  auto finish_pending = [&]() {
+    const unsigned long long excl = warp_sum_u64(static_cast<unsigned long long>(p_va & ~kTileReady) +
+                                                 (p_vb & ~kTileReady) + (p_vc & kCountBits));
+    if (p_t == num_tiles - 1 && lane == 0) *a.count_out = excl + p_agg;
+    write_tile(p_t, p_fb, p_bits, excl);
+    p_t = -1;
+  };
+
   for (;; st = (st + 1 == nst) ? 0 : st + 1, phase ^= (st == 0) ? 1u : 0u) {
     const long long c = my_chunk[st];
     if (c < 0) break;
@@ -201,6 +316,7 @@ __global__ void __launch_bounds__(kThreads) hc_dense_single_pass_kernel(const Se
       lane_cnt = 0;
       stepbits = 0;
     }
+    uint16_t* cur_flags = flags + fb * fstride;
     const uint8_t* sb = stages + static_cast<size_t>(st) * a.stage_bytes;
     // window starts of this chunk that exist: [vlo, vhi) relative to cC - head
     const long long cw0 = c * static_cast<long long>(C) - head;
@@ -248,7 +364,7 @@ __global__ void __launch_bounds__(kThreads) hc_dense_single_pass_kernel(const Se
       if (!filter_passes) m16 = 0u;
       if (__ballot_sync(0xffffffffu, m16 != 0u) == 0u) continue;
       const int s = k * steps_per_chunk + j;  // step within the tile
-      if (HC_IN_BOUNDS(s < a.flag_steps)) flags[s * 32 + lane] = static_cast<uint16_t>(m16);
+      if (HC_IN_BOUNDS(s < a.flag_steps)) cur_flags[s * 32 + lane] = static_cast<uint16_t>(m16);
       lane_cnt += static_cast<uint32_t>(__popc(m16));
       stepbits |= 1ull << s;
     }
@@ -264,72 +380,42 @@ __global__ void __launch_bounds__(kThreads) hc_dense_single_pass_kernel(const Se
       issue(st, next_chunk());
     }
     __syncwarp();
+    push_group();
+    // the pending tile's positions, once its prefix is complete
+    if (p_t >= 0 && prefix_ready()) finish_pending();
     if (k + 1 < tile_chunks(t)) continue;
 
-    // ---- the tile is scanned: publish, look back, write ----
+    // ---- tile t is scanned: its count into its entry and its group ----
     const unsigned long long agg = warp_sum_u64(static_cast<unsigned long long>(lane_cnt));
-    if (lane == 0)
-      st_relaxed_u64(a.lb_desc + t, (t == 0 ? kDescInclusive : kDescAggregate) | agg);
-    unsigned long long excl = 0;
-    if (t > 0) {
-      long long top = t - 1;  // lane l reads descriptor top - l
-      uint64_t t0 = 0;        // start of the current wait
-      uint32_t spins = 0;     // reads of the current wait
-      for (;;) {
-        const long long idx = top - lane;
-        unsigned long long dsc = kDescInclusive;  // before tile 0: inclusive count 0
-        if (idx >= 0) dsc = ld_relaxed_u64(a.lb_desc + idx);
-        const unsigned incl_lanes = __ballot_sync(0xffffffffu, (dsc >> 62) == 2ull);
-        const unsigned empty_lanes = __ballot_sync(0xffffffffu, (dsc >> 62) == 0ull);
-        // lanes up to and including the nearest inclusive descriptor
-        const unsigned need = incl_lanes ? ((incl_lanes & (0u - incl_lanes)) << 1) - 1u : 0xffffffffu;
-        if ((empty_lanes & need) == 0u) {
-          const unsigned long long v = ((need >> lane) & 1u) ? (dsc & kDescCount) : 0ull;
-          excl += warp_sum_u64(v);
-          if (incl_lanes) break;
-          top -= 32;
-          spins = 0;
-          continue;
-        }
-        // a tile claimed earlier has not published its count yet: wait
-        // (bounded; give up at once if another wait already gave up)
-        if (spins++ == 0) t0 = global_timer_ns();
-        bool give_up = false;
-        if ((spins & 63u) == 0u) {
-          give_up = global_timer_ns() - t0 > kWaitLimitNs || spins >= kMaxSpins ||
-                    (ld_relaxed_u32(a.status) & 1u) != 0u;
-        }
-        if (__any_sync(0xffffffffu, give_up)) {
-          if (lane == 0) atomicOr(a.status, 1u);
-          ok = false;
-          refilled = true;  // buffer st already holds the next chunk
-          break;
-        }
-      }
-      if (lane == 0) st_relaxed_u64(a.lb_desc + t, kDescInclusive | (excl + agg));
+    if (lane == 0) {
+      st_relaxed_u32(a.lb_desc + t, kTileReady | static_cast<unsigned int>(agg));
+      g_idx = static_cast<unsigned int>(t) / kGroupTiles;
+      g_size = static_cast<unsigned int>(min(static_cast<unsigned long long>(kGroupTiles), a.num_tiles - static_cast<unsigned long long>(g_idx) * kGroupTiles));
+      g_agg = agg;
+      g_old = atomicAdd(a.lb_gpack + g_idx, kOneAdded | agg);
+      g_pending = true;
     }
-    if (t == num_tiles - 1 && lane == 0) *a.count_out = excl + agg;
-
-    // positions of the tile, in text order: steps, then lanes, then windows
-    const long long tile_w0 = t * TC * static_cast<long long>(C) - head;
-    unsigned long long run = excl;
-    for (unsigned long long sbits = stepbits; sbits; sbits &= sbits - 1) {
-      const int s = __ffsll(static_cast<long long>(sbits)) - 1;
-      uint32_t m16 = HC_IN_BOUNDS(s < a.flag_steps) ? flags[s * 32 + lane] : 0u;
-      const uint32_t mine = static_cast<uint32_t>(__popc(m16));
-      const uint32_t incl = warp_incl_scan_u32(mine);
-      unsigned long long o = run + (incl - mine);
-      const unsigned long long pbase = static_cast<unsigned long long>(tile_w0 + (static_cast<long long>(s) << 9) + 16 * lane);
-      for (; m16; m16 &= m16 - 1u, ++o) {
-        if (o >= a.cap) break;
-        const unsigned long long p = pbase + static_cast<unsigned>(__ffs(m16) - 1);
-        if (a.pos32) reinterpret_cast<uint32_t*>(a.pos)[o] = static_cast<uint32_t>(p);
-        else a.pos[o] = p;
+    // the next tile takes the pending tile's flag buffer: write that one first
+    if (p_t >= 0) {
+      if (!wait_prefix()) {
+        ok = false;
+        refilled = true;
+        break;
       }
-      run += __shfl_sync(0xffffffffu, incl, 31);
+      finish_pending();
     }
-    if (!ok) break;
-    __syncwarp();  // the flag buffer is free for the next tile
+    p_t = t;
+    p_fb = fb;
+    p_bits = stepbits;
+    p_agg = agg;
+    start_prefix(t);
+    fb ^= 1;
+    __syncwarp();
+  }
+  push_group();
+  if (ok && p_t >= 0) {
+    if (wait_prefix()) finish_pending();
+    else ok = false;  // every chunk was consumed: no copy is in flight
   }
 
   if (!ok) {

@@ -24,7 +24,8 @@ constexpr int kEmitSplit = 2;               // CTAs of the emit kernel per recor
 constexpr int kMaxEmitGroup = 64;           // records per emit record group, at most
 constexpr int kEmitUnits = 8;               // 8-byte region loads in flight per emit thread
 constexpr int kSinglePassMaxSteps = 64;     // 512-window steps per single-pass tile (a u64 of flags)
-constexpr int kSinglePassTileSteps = 32;    // default steps per single-pass tile
+constexpr int kSinglePassTileSteps = 16;    // default steps per single-pass tile
+constexpr unsigned long long kSinglePassGroup = 64;  // tiles per group of the single-pass counts
 
 
 // Bytes of one staging buffer: head (< 16) + C + m - 1 bytes of text rounded
@@ -51,7 +52,8 @@ struct SearchArgs {
   unsigned long long* count_out;
   // workspace (no zeroing needed: the scan kernel writes every entry it or
   // the emit kernel reads)
-  unsigned long long* cta_total;     // [grid] occurrences in CTA b's range
+  unsigned long long* cta_total;     // [records] occurrences in record (warp) w's range
+  unsigned long long* blk_total;     // [grid] sum over CTA b's kWarps records (NULL: not kept)
   unsigned long long* cta_overflow;  // [grid] (first unstored chunk << 40) | stored, or kNoOverflow
   uint32_t* region;                  // [grid * region_entries] offsets from range start
   unsigned long long region_entries;
@@ -71,12 +73,15 @@ struct SearchArgs {
   uint32_t w0, w1;
   int g0;
   // single-pass dense form (m = q): tiles of tile_chunks consecutive chunks
-  // are claimed in order from *lb_ticket; lb_desc[t] carries tile t's
-  // aggregate or inclusive count (see hc_dense.cu); flag_steps is the number
-  // of 512-window steps per tile (the per-warp flag buffer in shared memory)
+  // are claimed from the kWarps counters at lb_ticket; lb_desc[t] holds tile
+  // t's match count, lb_gpack[g] the total of group g (64 tiles) and
+  // lb_gtree[1..G] a Fenwick tree of the group totals (see hc_dense.cu);
+  // flag_steps is the number of 512-window steps per tile
   unsigned int* lb_ticket;
-  unsigned long long* lb_desc;
-  unsigned long long num_tiles;
+  unsigned int* lb_desc;
+  unsigned long long* lb_gpack;
+  unsigned long long* lb_gtree;
+  unsigned long long num_tiles, num_groups;
   int tile_chunks;
   int flag_steps;
 };
@@ -148,6 +153,60 @@ __device__ __forceinline__ uint32_t qgram_hash(const uint8_t* base, int o, const
   load_qgram<Q, STAGED>(base, o, &lo, &hi);
   return hash_bytes<Q>(lo, hi, a);
 }
+
+// ---------------------------------------------------------------------------
+// Byte tests of the dense (m = q) scans: 16 consecutive windows per lane,
+// four per 32-bit word (byte k of a word belongs to window 4g + k).
+
+// Bytes at lane-relative offset off .. off+3 of the 24 bytes Tw holds.
+template <int OFF>
+__device__ __forceinline__ uint32_t text_word(const uint32_t (&Tw)[6]) {
+  if constexpr ((OFF & 3) == 0) return Tw[OFF >> 2];
+  else return __funnelshift_r(Tw[OFF >> 2], Tw[(OFF >> 2) + 1], 8u * (OFF & 3));
+}
+
+// Column set of the byte test: 0 = every column c < Q; 1 = the first
+// stage of the two-stage test (columns 0, 1, 4, 5: the cheapest four, two
+// of them word-aligned); 2 = the remaining columns.
+template <int SET>
+__device__ __forceinline__ constexpr bool in_set(int c) {
+  return SET == 0 || ((SET == 1) == ((c & 2) == 0));
+}
+
+// d[g] |= OR over the columns c of SET of (text bytes at 4g + c) ^ x[c]
+// replicated: byte k of d[g] stays 0 while window 4g + k agrees with x on
+// those columns.
+template <int Q, int SET, int G, int C>
+__device__ __forceinline__ void or_columns(const uint32_t (&Tw)[6], const uint32_t (&xrep)[Q],
+                                           uint32_t (&d)[4]) {
+  if constexpr (C < Q) {
+    if constexpr (in_set<SET>(C)) d[G] |= text_word<4 * G + C>(Tw) ^ xrep[C];
+    or_columns<Q, SET, G, C + 1>(Tw, xrep, d);
+  } else if constexpr (G < 3) {
+    or_columns<Q, SET, G + 1, 0>(Tw, xrep, d);
+  }
+}
+
+// Bit 7 of byte k of the result is set iff byte k of d is zero (exact for
+// every byte).
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t d) {
+  return ~(((d & 0x7f7f7f7fu) + 0x7f7f7f7fu) | d | 0x7f7f7f7fu);
+}
+
+// Nonzero iff d has a zero byte (the lowest zero byte is always flagged;
+// bytes above it may be flagged wrongly, so only the test is used).
+__device__ __forceinline__ uint32_t has_zero_byte(uint32_t d) {
+  return (d - 0x01010101u) & ~d & 0x80808080u;
+}
+
+// 16-bit mask, bit 4g + k set iff bit 8k + 7 of z[g] is set.
+__device__ __forceinline__ uint32_t gather_mask(const uint32_t (&z)[4]) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) m |= (((z[g] >> 7) * 0x01020408u) >> 24) << (4 * g);
+  return m;
+}
+
 
 // Whether the m bytes of a window starting at chunk-relative `start` may be
 // read for verification (always true outside checked builds).
@@ -414,6 +473,23 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
   return cnt;
 }
 
+// End of a single-search scan CTA: the sum of its kWarps records' totals
+// (each written by lane 0 of its warp) into blk_total[blockIdx.x], so that
+// the emit kernel sums one total per CTA instead of one per warp.  Every
+// thread of the CTA must call it.
+__device__ __forceinline__ void block_total(const SearchArgs& a) {
+  __shared__ unsigned long long s_wt[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_wt[warp] = a.cta_total[static_cast<unsigned long long>(blockIdx.x) * kWarps + warp];
+  __syncthreads();
+  if (threadIdx.x == 0 && a.blk_total != nullptr) {
+    unsigned long long t = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += s_wt[w];
+    a.blk_total[blockIdx.x] = t;
+  }
+}
+
 // Block-wide exclusive scan of one count per thread; every thread gets its
 // exclusive prefix and the block total.  Uses warp_sum (kWarps words).
 __device__ __forceinline__ void block_scan(uint32_t cnt, uint32_t* warp_sum, uint32_t* excl,
@@ -584,17 +660,25 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
   const unsigned long long r1 = min(r0 + a.emit_group, a.records);
 
   __shared__ unsigned long long s_tot[kMaxEmitGroup], s_ovf[kMaxEmitGroup];
-  // sum of the earlier records' totals: loads issued 8 at a time
   unsigned long long p = 0;
-  for (unsigned long long k0 = tid; k0 < r0; k0 += 8ull * kThreads) {
-    unsigned long long v[8];
+  if (a.blk_total != nullptr) {
+    // sum of the earlier records' totals: the CTAs wholly before record r0
+    // (one total each), then the records of r0's CTA before it
+    const unsigned long long b0 = r0 / kWarps;
+    for (unsigned long long k = tid; k < b0; k += kThreads) p += a.blk_total[k];
+    for (unsigned long long k = b0 * kWarps + tid; k < r0; k += kThreads) p += a.cta_total[k];
+  } else {
+    // sum of the earlier records' totals: loads issued 8 at a time
+    for (unsigned long long k0 = tid; k0 < r0; k0 += 8ull * kThreads) {
+      unsigned long long v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const unsigned long long k = k0 + static_cast<unsigned long long>(u) * kThreads;
-      v[u] = k < r0 ? a.cta_total[k] : 0ull;
+      for (int u = 0; u < 8; ++u) {
+        const unsigned long long k = k0 + static_cast<unsigned long long>(u) * kThreads;
+        v[u] = k < r0 ? a.cta_total[k] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) p += v[u];
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) p += v[u];
   }
   p = warp_sum_u64(p);
   if (lane == 0) red[warp] = p;

@@ -25,11 +25,12 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB per device
 constexpr unsigned long long kNoAllocMaxPositions = 2000000ull;
-// The spill form's scratch is at most 32 bytes per record (16 of totals, up
-// to 16 of rounding of its region) plus 4 per held position; records are
-// capped so that any request within kNoAllocMaxPositions fits.
+// The spill form's scratch is at most 33 bytes per record (16 of totals, up
+// to 16 of rounding of its region, 1 of its CTA's total) plus 4 per held
+// position; records are capped so that any request within
+// kNoAllocMaxPositions fits.
 constexpr unsigned long long kNoAllocMaxRecords =
-    (kNoAllocScratchBytes - 4 * kNoAllocMaxPositions) / 32;
+    (kNoAllocScratchBytes - 4 * kNoAllocMaxPositions) / 40;
 
 // Scratch of hc_search_noalloc: per-CTA totals and overflow marks, then the
 // per-CTA spill regions.  Every entry the kernels read is written by the

@@ -71,10 +71,16 @@ __global__ void __launch_bounds__(kThreads, STAGED ? 4 : 5) hc_scan_kernel(const
     xs[i] = a.x[i];
   const uint8_t* xv = a.x_smem ? xs : a.x;
   __syncthreads();
+  // launched as a programmatic dependent of the previous search's emit
+  // kernel: F and x (read above) are not written by it, but the text, the
+  // workspace (which may reuse the previous one's memory) and the outputs
+  // are touched only after that kernel has completed
+  pdl_wait();
   uint8_t* stages = reinterpret_cast<uint8_t*>(slots + kSlots * kThreads) +
                     static_cast<size_t>(warp) * a.stages * a.stage_bytes;
   warp_stream<Q, STAGED>(a, static_cast<unsigned long long>(blockIdx.x) * kWarps + warp, Fs, xv,
                          slots, stages, bars[warp]);
+  block_total(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -93,16 +99,9 @@ __global__ void __launch_bounds__(kThreads, STAGED ? 4 : 5) hc_scan_kernel(const
 // its matches -- compacted in order with ballots -- straight to its own
 // spill region.  There is no CTA-wide barrier in the loop.
 template <int Q>
-__global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArgs a) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
-  pdl_launch_dependents();
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem, uint64_t* wb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned long long w_id = static_cast<unsigned long long>(blockIdx.x) * kWarps + warp;
-  uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
-  for (uint32_t i = tid; i < a.fwords; i += kThreads) Fs[i] = a.F[i];
-  __syncthreads();
 
   const unsigned long long c0 = w_id * a.chunks_per_cta;
   const unsigned long long c1 = min(c0 + a.chunks_per_cta, a.num_chunks);
@@ -114,9 +113,7 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
     return;
   }
   const int nst = a.stages;
-  const uint32_t f_bytes = (a.fwords * 4u + 15u) & ~15u;
-  uint8_t* stages = smem + f_bytes + static_cast<size_t>(warp) * nst * a.stage_bytes;
-  uint64_t* wb = bars[warp];
+  uint8_t* stages = smem + static_cast<size_t>(warp) * nst * a.stage_bytes;
   const int nchunks = static_cast<int>(c1 - c0);
 
   // the chunk's bytes go to stage (i % nst); the warp's lane 0 drives the copies
@@ -143,9 +140,12 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
     xrep[c] = 0x01010101u * xb;
     if (c < 4) xlo |= xb << (8 * c); else xhi |= xb << (8 * (c - 4));
   }
-  // HC's first test and H_v test, evaluated on x itself (see above)
+  // HC's first test and H_v test, evaluated on x itself (see above); F
+  // itself is read once from global memory (it is not staged: nothing else
+  // of it is needed)
   const uint32_t hx = hash_bytes<Q>(xlo, xhi, a);
-  const bool filter_passes = Fs[hx] != 0u && hx == a.hv;
+  const bool filter_passes = __ldg(a.F + hx) != 0u && hx == a.hv;
+  int single_left = 0;  // chunks left in the one-stage byte test (q >= 5)
 
   const unsigned long long S = a.region_entries;
   uint32_t* region = a.region + w_id * S;
@@ -175,35 +175,43 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
     // window grid shifted by -head so that every lane's 16 windows start at a
     // 16-byte aligned shared-memory offset; windows outside [0, wins) are
     // masked
+    // q >= 5: a two-stage byte test (columns 0, 1, 4, 5 first; the others
+    // only in steps where some lane has a candidate) while the first stage
+    // rejects most steps, else the one-stage test for the next 16 chunks
+    const bool two = Q >= 5 && single_left == 0;
+    int second = 0, steps = 0;
     for (int base = -a.head; base < wins; base += 512) {
+      ++steps;
       const int w0 = base + 16 * lane;      // first window of this lane
-      uint32_t dg[4] = {~0u, ~0u, ~0u, ~0u};
+      uint32_t dg[4] = {0u, 0u, 0u, 0u};
+      uint32_t Tw[6] = {0u, 0u, 0u, 0u, 0u, 0u};
       uint32_t cand = 0;
       // lanes past the chunk's end read nothing
-      if (w0 < wins && HC_IN_BOUNDS(a.head + w0 >= 0 && static_cast<uint32_t>(a.head + w0) + 24u <= a.stage_bytes)) {
+      const bool live = w0 < wins && HC_IN_BOUNDS(a.head + w0 >= 0 && static_cast<uint32_t>(a.head + w0) + 24u <= a.stage_bytes);
+      if (live) {
         const uint32_t o = static_cast<uint32_t>(a.head + w0);
         const uint4 A = *reinterpret_cast<const uint4*>(sb + o);
         const uint2 B = *reinterpret_cast<const uint2*>(sb + o + 16);
-        const uint32_t Tw[6] = {A.x, A.y, A.z, A.w, B.x, B.y};  // bytes o .. o+23
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          // byte k of d stays 0 while window w0+4g+k agrees with x
-          uint32_t d = Tw[g] ^ xrep[0];
-#pragma unroll
-          for (int cc = 1; cc < Q; ++cc) {
-            const int wq = g + (cc >> 2);
-            const uint32_t col = (cc & 3) ? __funnelshift_r(Tw[wq], Tw[wq + 1], 8u * (cc & 3)) : Tw[wq];
-            d |= col ^ xrep[cc];
-          }
-          dg[g] = d;
-          // nonzero iff d has a zero byte (exact for the word; the flag
-          // positions above a zero byte may be wrong, so they are not used)
-          cand |= (d - 0x01010101u) & ~d & 0x80808080u;
-        }
+        Tw[0] = A.x; Tw[1] = A.y; Tw[2] = A.z; Tw[3] = A.w; Tw[4] = B.x; Tw[5] = B.y;  // bytes o .. o+23
+        // byte k of dg[g] stays 0 while window w0+4g+k agrees with x
+        if (two) or_columns<Q, 1, 0, 0>(Tw, xrep, dg);
+        else or_columns<Q, 0, 0, 0>(Tw, xrep, dg);
+        // nonzero iff some dg[g] has a zero byte (exact for the word; the
+        // flag positions above a zero byte may be wrong, so they are not used)
+        cand = has_zero_byte(dg[0]) | has_zero_byte(dg[1]) | has_zero_byte(dg[2]) | has_zero_byte(dg[3]);
         if (!filter_passes) cand = 0;
       }
-      const uint32_t cand_lanes = __ballot_sync(0xffffffffu, cand != 0u);
+      uint32_t cand_lanes = __ballot_sync(0xffffffffu, cand != 0u);
       if (cand_lanes == 0u) continue;
+      if (two) {
+        ++second;
+        if (live && cand != 0u) {
+          or_columns<Q, 2, 0, 0>(Tw, xrep, dg);
+          cand = has_zero_byte(dg[0]) | has_zero_byte(dg[1]) | has_zero_byte(dg[2]) | has_zero_byte(dg[3]);
+        }
+        cand_lanes = __ballot_sync(0xffffffffu, cand != 0u);
+        if (cand_lanes == 0u) continue;
+      }
       // exact zero-byte test: bit 8k+7 of zg[g] is set iff window w0+4g+k
       // equals x (bit 7 of a byte set iff the byte is 0)
       uint32_t zg[4] = {0u, 0u, 0u, 0u};
@@ -260,6 +268,10 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
       }
       t += __shfl_sync(0xffffffffu, incl, 31);
     }
+    if (Q >= 5) {
+      if (two && 2 * second > steps) single_left = 16;
+      else if (!two) --single_left;
+    }
     if (store && t > S) overflow = (static_cast<unsigned long long>(i) << 40) | T;
     T = t;
     __syncwarp();  // staging buffer st is free again
@@ -277,6 +289,19 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
   }
 }
 
+template <int Q>
+__global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
+  pdl_launch_dependents();
+  // launched as a programmatic dependent of the previous search's emit
+  // kernel: nothing of memory is touched before that kernel has completed
+  // (only the launch and the CTAs' start overlap its tail)
+  pdl_wait();
+  dense_stream<Q>(a, smem, bars[threadIdx.x >> 5]);
+  block_total(a);
+}
+
 // ---------------------------------------------------------------------------
 // Kernel 2: record r's output offset is the sum of cta_total[0..r); copy its
 // region to the output; re-scan (from global memory) the chunks whose
@@ -287,6 +312,7 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
 template <int Q>
 __global__ void __launch_bounds__(kThreads, 4) hc_emit_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
+  pdl_launch_dependents();  // the next search's scan may be scheduled; it waits for this grid
   pdl_wait();  // the scan grid has completed and its records are visible
   emit_group<Q>(a, blockIdx.x / kEmitSplit, blockIdx.x % kEmitSplit, smem);
 }
@@ -447,7 +473,7 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   if (sp_opt < -1 || sp_opt > 1) return set_error(HC_ERR_ARG, "hc_search: single_pass out of [-1, 1]");
   if (tile_steps_opt < 0 || tile_steps_opt > kSinglePassMaxSteps)
     return set_error(HC_ERR_ARG, "hc_search: tile_steps out of [0, 64]");
-  if (kind == HC_MODE_DENSE && sp_opt >= 0) {
+  if (kind == HC_MODE_DENSE && sp_opt == 1) {
     // single pass: chunks of a whole number of 512-window steps (L even),
     // tiles of whole chunks, at most kSinglePassMaxSteps steps per tile
     const int Ls = std::max(2, (L + 1) & ~1);
@@ -463,8 +489,9 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
       p.stage_bytes = stage_bytes_for(p.C, f->m, true);
       p.scan = dense_single_pass_kernel_for_q(f->q);
       p.init = single_pass_init_kernel();
-      // per warp: its ring of staging buffers and its step masks (u16 per lane)
-      p.smem_scan = size_t(kWarps) * stages * p.stage_bytes + size_t(kWarps) * p.flag_steps * 64;
+      // per warp: its ring of staging buffers and two tiles' step masks (u16
+      // per lane and step: the tile being scanned, the one being written)
+      p.smem_scan = size_t(kWarps) * stages * p.stage_bytes + size_t(kWarps) * 2 * p.flag_steps * 64;
       if (p.smem_scan + static_smem(p.scan) > di.smem_optin) p.single_pass = false;
     } else if (sp_opt == 1) {
       return set_error(HC_ERR_ARG, "hc_search: single pass needs at most 64 steps of 512 windows per tile");
@@ -481,7 +508,7 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   if (kind == HC_MODE_DENSE && !p.single_pass) {
     // one ring of `stages` buffers per warp
     p.scan = dense_kernel_for_q(f->q);
-    p.smem_scan = fbytes + size_t(kWarps) * stages * p.stage_bytes;
+    p.smem_scan = size_t(kWarps) * stages * p.stage_bytes;  // F is not staged
     if (mode == HC_MODE_AUTO && p.smem_scan + static_smem(p.scan) > di.smem_optin) {
       kind = HC_MODE_STAGED;  // caller's lane_bytes too large for per-warp rings
       p.C = 32u * static_cast<uint32_t>(L);
@@ -528,13 +555,17 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
     // 16 < 16); a persistent grid of at most one wave of warps claims tiles
     const unsigned long long chunks = (nwin + 15 + p.C - 1) / p.C;
     p.max_tiles = (chunks + p.tile_chunks - 1) / p.tile_chunks;
+    if (p.max_tiles >= (1ull << 30))
+      return set_error(HC_ERR_ARG, "hc_search: text too long for the single-pass form (use single_pass = -1)");
     p.num_chunks = chunks;
     p.grid = std::min<unsigned long long>(static_cast<unsigned long long>(per_sm) * di.sm_count,
                                           (p.max_tiles + kWarps - 1) / kWarps);
     p.records = 0;
     p.emit = nullptr;
     p.emit_ctas = 0;
-    p.ws_bytes = p.max_tiles * 8 + 16;
+    // tile entries, group totals, group tree (nodes 0..G), tile counters
+    const unsigned long long groups = (p.max_tiles + kSinglePassGroup - 1) / kSinglePassGroup;
+    p.ws_bytes = (2 * groups + 1) * 8 + (p.max_tiles + kWarps) * 4;
     *out = p;
     return HC_OK;
   }
@@ -560,7 +591,7 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
       std::min<unsigned long long>(p.records, 2ull * di.sm_count));
   p.emit_group = (p.records + groups - 1) / groups;
   p.emit_ctas = ((p.records + p.emit_group - 1) / p.emit_group) * kEmitSplit;
-  p.ws_bytes = p.records * 16 + p.records * p.region_entries * 4;
+  p.ws_bytes = p.records * 16 + p.records * p.region_entries * 4 + p.grid * 8;
   *out = p;
   return HC_OK;
 }
@@ -604,14 +635,19 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   a.cap = pos ? cap : 0;
   a.count_out = reinterpret_cast<unsigned long long*>(count_dev);
   if (p.single_pass) {
-    a.lb_desc = static_cast<unsigned long long*>(ws);
-    a.lb_ticket = reinterpret_cast<unsigned int*>(a.lb_desc + p.max_tiles);
+    const unsigned long long groups = (p.max_tiles + kSinglePassGroup - 1) / kSinglePassGroup;
+    a.lb_gpack = static_cast<unsigned long long*>(ws);
+    a.lb_gtree = a.lb_gpack + groups;
+    a.lb_desc = reinterpret_cast<unsigned int*>(a.lb_gtree + groups + 1);
+    a.lb_ticket = a.lb_desc + p.max_tiles;
     a.tile_chunks = p.tile_chunks;
     a.flag_steps = p.flag_steps;
   } else {
     a.cta_total = static_cast<unsigned long long*>(ws);
     a.cta_overflow = a.cta_total + p.records;
     a.region = reinterpret_cast<uint32_t*>(a.cta_overflow + p.records);
+    // after the regions (R * S * 4 bytes, S a multiple of 4: 16-byte aligned)
+    a.blk_total = reinterpret_cast<unsigned long long*>(a.region + p.records * p.region_entries);
   }
   a.region_entries = p.region_entries;
   a.num_chunks = p.num_chunks;
@@ -622,6 +658,7 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   if (p.single_pass) {
     a.num_chunks = (a.nwin + static_cast<unsigned long long>(a.head) + p.C - 1) / p.C;
     a.num_tiles = (a.num_chunks + p.tile_chunks - 1) / p.tile_chunks;
+    a.num_groups = (a.num_tiles + kSinglePassGroup - 1) / kSinglePassGroup;
   }
   a.stage_bytes = p.stage_bytes;
   a.x_smem = p.x_smem;
@@ -666,8 +703,12 @@ static int launch_args(const SearchPlan& p, const SearchArgs& a, cudaStream_t st
     return HC_OK;
   }
   TimingToken t0 = timing_begin(kind, stream);
-  p.scan<<<static_cast<unsigned>(p.grid), kThreads, p.smem_scan, stream>>>(a);
-  e = cudaGetLastError();
+  // a programmatic dependent of whatever kernel precedes it in the stream:
+  // only this library's emit kernel lets a dependent start early, and the
+  // scan waits for it before touching memory
+  e = launch_dependent(p.scan, static_cast<unsigned>(p.grid), kThreads, p.smem_scan, stream,
+                       !t0.active(), a);
+  if (e == cudaSuccess) e = cudaGetLastError();
   timing_end(t0, stream);
   if (e != cudaSuccess) return cuda_error(e, "hc_scan_kernel launch");
   TimingToken t1 = timing_begin(kKindEmit, stream);

@@ -174,14 +174,18 @@ int grow_pinned(T** p, size_t* cap, size_t need, unsigned flags, const char* wha
 }  // namespace
 
 // Takes the next batch from the queue (lock held): queue order, at most
-// max_batch requests, admitted memory within the limit, the combined
+// max_batch requests and max_batch_bytes of text (a lone larger request
+// still forms a batch), admitted memory within the limit, the combined
 // shared-memory layout within one CTA.
 std::vector<Req*> Server::take_batch() {
   std::vector<Req*> b;
   BatchLayout lay{};
   const size_t optin = device_info(dev).smem_optin;
+  uint64_t text_bytes = 0;  // of the batch: bounded so that a backlog is cut into several
+                            // batches that run on several streams and finish one by one
   while (!pending.empty() && b.size() < static_cast<size_t>(cfg.max_batch)) {
     Req* r = pending.front();
+    if (!b.empty() && text_bytes + r->n > cfg.max_batch_bytes) break;
     if (r->dev_bytes > request_limit()) {  // can never be admitted
       pending.pop_front();
       r->status = HC_ERR_ADMISSION;
@@ -202,6 +206,7 @@ std::vector<Req*> Server::take_batch() {
     if (!b.empty() && !layout_fits(nl, optin)) break;
     lay = nl;
     b.push_back(r);
+    text_bytes += r->n;
     inflight_bytes += r->dev_bytes;
     pending.pop_front();
   }
@@ -579,6 +584,7 @@ int hc_server_create(const hc_server_config* cfg_in, const hc_tuner* tuner, hc_s
   if (cfg.max_inflight == 0) cfg.max_inflight = 3;
   if (cfg.max_batch == 0) cfg.max_batch = 1024;
   if (cfg.default_cap == 0) cfg.default_cap = 4096;
+  if (cfg.max_batch_bytes == 0) cfg.max_batch_bytes = uint64_t(64) << 20;
   if (cfg.max_inflight < 1 || cfg.max_inflight > 16 || cfg.max_batch < 1 || cfg.max_batch > (1 << 20) ||
       cfg.default_cap > (uint64_t(1) << 32))
     return set_error(HC_ERR_ARG, "hc_server_create: max_inflight in [1, 16], max_batch in [1, 2^20], default_cap <= 2^32");

@@ -97,14 +97,15 @@ def test_traffic_record_belongs_to_its_workload(tmp_path, monkeypatch):
 def test_dense_single_pass_rule_matches_the_planner():
     """The bench counts a dense search's bytes as one pass (text + one write
     per position) exactly when the library's planner picks its single-pass
-    kernel: automatic or forced single pass within the tile and shared-memory
-    limits, the spill form when asked or when the tiles would not fit."""
+    kernel: single pass asked for, within the tile and shared-memory limits;
+    otherwise (the automatic choice) the spill form."""
     import paper_2310_15711_gb300 as hc
     import bench
-    assert bench.dense_single_pass(None, 4)
-    assert bench.dense_single_pass(hc.SearchOpts(lane_bytes=8), 8)
-    assert bench.dense_single_pass(hc.SearchOpts(lane_bytes=1, tile_steps=1), 2)
+    assert not bench.dense_single_pass(None, 4)                               # automatic: spill form
+    assert not bench.dense_single_pass(hc.SearchOpts(lane_bytes=8), 8)
+    assert bench.dense_single_pass(hc.SearchOpts(lane_bytes=8, single_pass=1), 8)
+    assert bench.dense_single_pass(hc.SearchOpts(lane_bytes=1, tile_steps=1, single_pass=1), 2)
     assert not bench.dense_single_pass(hc.SearchOpts(single_pass=-1), 4)
-    assert not bench.dense_single_pass(hc.SearchOpts(lane_bytes=256), 4)      # 128 steps per chunk
-    assert not bench.dense_single_pass(hc.SearchOpts(lane_bytes=64, tile_steps=64), 4)  # buffers too big
-    assert bench.dense_single_pass(hc.SearchOpts(lane_bytes=16, tile_steps=64), 4)
+    assert not bench.dense_single_pass(hc.SearchOpts(lane_bytes=256, single_pass=1), 4)   # 128 steps per chunk
+    assert not bench.dense_single_pass(hc.SearchOpts(lane_bytes=64, tile_steps=64, single_pass=1), 4)  # too big
+    assert bench.dense_single_pass(hc.SearchOpts(lane_bytes=16, tile_steps=64, single_pass=1), 4)

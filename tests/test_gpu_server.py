@@ -221,3 +221,28 @@ def test_bad_requests_rejected(hc):
         assert ei.value.code == hc.HC_ERR_ARG
     assert srv.stats()["submitted"] == 0
     srv.destroy()
+
+
+def test_batches_bounded_by_text_bytes(hc):
+    """A backlog submitted at once is cut into batches of at most
+    max_batch_bytes of text (a single larger request runs alone), which run on
+    several streams; every result still equals the oracle's."""
+    bound = 2_000_000
+    srv = hc.HCServer(hc.ServerConfig(max_batch_bytes=bound, max_batch=64))
+    ys, ids = _texts(srv)
+    rng = np.random.default_rng(77)
+    reqs = _requests(ys, 120, rng)
+    rq = [(ids[ti], x) for ti, x in reqs]
+    rids = srv.replay(rq, [0.0] * len(rq))
+    srv.drain()
+    res = _collect(srv, len(reqs))
+    _check(res, ys, dict(zip(rids, reqs)))
+    text_of = dict(zip(rids, (ti for ti, _ in reqs)))
+    per_batch, size_of = {}, {}
+    for r in res:
+        per_batch[r["batch"]] = per_batch.get(r["batch"], 0) + ys[text_of[r["id"]]].size
+        size_of[r["batch"]] = r["batch_size"]
+    assert all(v <= bound or size_of[b] == 1 for b, v in per_batch.items())
+    total = sum(ys[ti].size for ti, _ in reqs)
+    assert len(per_batch) >= total // bound
+    srv.destroy()

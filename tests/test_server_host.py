@@ -44,3 +44,17 @@ def test_null_server_rejected(hc):
     assert L.hc_server_get_stats(None, None) == hc.HC_ERR_ARG
     assert L.hc_server_replay(None, None, 0, None, None) == hc.HC_ERR_ARG
     L.hc_server_destroy(None)
+
+
+def test_config_struct_matches_the_header(hc):
+    """The binding's hc_server_config has the header's layout, including the
+    per-batch text bound (max_batch_bytes, last member); a configuration with
+    every field set is accepted by hc_server_create's checks (the server is
+    only created where a device exists)."""
+    import ctypes as C
+    fields = [f for f, _ in hc.ServerConfig._fields_]
+    assert fields[-1] == "max_batch_bytes"
+    cfg = hc.ServerConfig(max_batch_bytes=123 << 20, max_batch=10, max_inflight=4)
+    assert cfg.max_batch_bytes == 123 << 20 and cfg.struct_size == C.sizeof(hc.ServerConfig)
+    # the header's struct: size_t, u64, int, int, u64, int, int, u64
+    assert C.sizeof(hc.ServerConfig) == 8 + 8 + 4 + 4 + 8 + 4 + 4 + 8
