@@ -154,6 +154,38 @@ __device__ __forceinline__ uint32_t qgram_hash(const uint8_t* base, int o, const
   return hash_bytes<Q>(lo, hi, a);
 }
 
+// The hash constants of a search, held in registers by the per-lane scan
+// (read from the kernel's parameters once instead of inside its loops).
+struct HashK {
+  uint32_t w0, w1, mask, g8, sg;  // weights of the two byte groups, mask, 8*g0, s*g0
+};
+
+__device__ __forceinline__ HashK hash_consts(const SearchArgs& a) {
+  return HashK{a.w0, a.w1, a.mask, 8u * static_cast<uint32_t>(a.g0), static_cast<uint32_t>(a.s * a.g0)};
+}
+
+// hash_bytes with the constants in registers
+template <int Q>
+__device__ __forceinline__ uint32_t hash_k(uint32_t lo, uint32_t hi, const HashK& k) {
+  uint32_t v = __dp4a(lo, k.w0, 0u);
+  if constexpr (Q > 1) v += __dp4a(__funnelshift_rc(lo, hi, k.g8), k.w1, 0u) << k.sg;
+  return v & k.mask;
+}
+
+// qgram_hash with the constants in registers
+template <int Q, bool STAGED>
+__device__ __forceinline__ uint32_t qgram_hash_k(const uint8_t* base, int o, const SearchArgs& a,
+                                                 const HashK& k) {
+  if constexpr (STAGED) {
+    if (!HC_IN_BOUNDS(o >= 0 && o + 12 <= static_cast<int>(a.stage_bytes))) o = 0;
+  } else {
+    if (!HC_IN_BOUNDS(base + o >= a.y && base + o + Q <= a.y + a.n)) o = 0;
+  }
+  uint32_t lo, hi;
+  load_qgram<Q, STAGED>(base, o, &lo, &hi);
+  return hash_k<Q>(lo, hi, k);
+}
+
 // ---------------------------------------------------------------------------
 // Byte tests of the dense (m = q) scans: 16 consecutive windows per lane,
 // four per 32-bit word (byte k of a word belongs to window 4g + k).
@@ -197,6 +229,15 @@ __device__ __forceinline__ uint32_t zero_bytes(uint32_t d) {
 // bytes above it may be flagged wrongly, so only the test is used).
 __device__ __forceinline__ uint32_t has_zero_byte(uint32_t d) {
   return (d - 0x01010101u) & ~d & 0x80808080u;
+}
+
+// Nonzero iff some word of d has a zero byte (the per-word test of
+// has_zero_byte, the four words combined before the final mask).
+__device__ __forceinline__ uint32_t any_zero_byte4(const uint32_t (&d)[4]) {
+  uint32_t acc = 0;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) acc |= (d[g] - 0x01010101u) & ~d[g];
+  return acc & 0x80808080u;
 }
 
 // 16-bit mask, bit 4g + k set iff bit 8k + 7 of z[g] is set.
@@ -380,6 +421,7 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
   const uint32_t hv = a.hv;
   const int shift = m - Q + 1;
   const uint8_t* txt = base + head;
+  const HashK hk = hash_consts(a);
   int cnt = 0;
   int e = lo + m - 1;              // window end (chunk-relative)
   const int e_end = hi + m - 1;    // first window end past the segment
@@ -401,7 +443,7 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
         for (int u = 0; u < kFirstTests; ++u) {
           const int ek = e + u * shift;
           const bool in = u == 0 || ek < e_end;
-          vu[u] = qgram_hash<Q, STAGED>(base, head + (in ? ek : e) - Q + 1, a);
+          vu[u] = qgram_hash_k<Q, STAGED>(base, head + (in ? ek : e) - Q + 1, a, hk);
           zu[u] = in ? Fs[vu[u]] : 0u;
         }
         int k = kFirstTests;
@@ -430,7 +472,7 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
           break;
         }
         j -= Q;
-        v = qgram_hash<Q, STAGED>(base, head + j - Q + 1, a);
+        v = qgram_hash_k<Q, STAGED>(base, head + j - Q + 1, a, hk);
         if ((z & (1u << (v & 31u))) == 0) {
           broke = true;
           break;

@@ -180,37 +180,43 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
     // rejects most steps, else the one-stage test for the next 16 chunks
     const bool two = Q >= 5 && single_left == 0;
     int second = 0, steps = 0;
-    for (int base = -a.head; base < wins; base += 512) {
-      ++steps;
+    // The first (or only) stage of the byte test for the step at `base`
+    // (512 windows, 16 per lane): Tw and dg receive the lane's text words
+    // and column differences; returns the lane's candidate flags.  Lanes
+    // past the chunk's end read the buffer's last 32 bytes instead (no
+    // branch; a 16-byte aligned offset, as every lane's is) and discard what
+    // they find.
+    auto test = [&](int base, uint32_t (&Tw)[6], uint32_t (&dg)[4]) -> uint32_t {
       const int w0 = base + 16 * lane;      // first window of this lane
-      uint32_t dg[4] = {0u, 0u, 0u, 0u};
-      uint32_t Tw[6] = {0u, 0u, 0u, 0u, 0u, 0u};
-      uint32_t cand = 0;
-      // lanes past the chunk's end read nothing
-      const bool live = w0 < wins && HC_IN_BOUNDS(a.head + w0 >= 0 && static_cast<uint32_t>(a.head + w0) + 24u <= a.stage_bytes);
-      if (live) {
-        const uint32_t o = static_cast<uint32_t>(a.head + w0);
-        const uint4 A = *reinterpret_cast<const uint4*>(sb + o);
-        const uint2 B = *reinterpret_cast<const uint2*>(sb + o + 16);
-        Tw[0] = A.x; Tw[1] = A.y; Tw[2] = A.z; Tw[3] = A.w; Tw[4] = B.x; Tw[5] = B.y;  // bytes o .. o+23
-        // byte k of dg[g] stays 0 while window w0+4g+k agrees with x
-        if (two) or_columns<Q, 1, 0, 0>(Tw, xrep, dg);
-        else or_columns<Q, 0, 0, 0>(Tw, xrep, dg);
-        // nonzero iff some dg[g] has a zero byte (exact for the word; the
-        // flag positions above a zero byte may be wrong, so they are not used)
-        cand = has_zero_byte(dg[0]) | has_zero_byte(dg[1]) | has_zero_byte(dg[2]) | has_zero_byte(dg[3]);
-        if (!filter_passes) cand = 0;
-      }
-      uint32_t cand_lanes = __ballot_sync(0xffffffffu, cand != 0u);
-      if (cand_lanes == 0u) continue;
+      const bool live = w0 < wins;
+      const uint32_t o = min(static_cast<uint32_t>(a.head + w0), a.stage_bytes - 32u);
+      HC_IN_BOUNDS(static_cast<uint32_t>(a.head + w0) + 24u <= a.stage_bytes || !live);
+      const uint4 A = *reinterpret_cast<const uint4*>(sb + o);
+      const uint2 B = *reinterpret_cast<const uint2*>(sb + o + 16);
+      Tw[0] = A.x; Tw[1] = A.y; Tw[2] = A.z; Tw[3] = A.w; Tw[4] = B.x; Tw[5] = B.y;  // bytes o .. o+23
+      // byte k of dg[g] stays 0 while window w0+4g+k agrees with x
+      dg[0] = dg[1] = dg[2] = dg[3] = 0u;
+      if (two) or_columns<Q, 1, 0, 0>(Tw, xrep, dg);
+      else or_columns<Q, 0, 0, 0>(Tw, xrep, dg);
+      // nonzero iff some dg[g] has a zero byte (exact for the test; the flag
+      // positions above a zero byte may be wrong, so they are not used)
+      return (live && filter_passes) ? any_zero_byte4(dg) : 0u;
+    };
+    // The rest of a step in which some lane has a candidate: the second
+    // stage, the exact per-window flags and the ordered writes.
+    auto finish_step = [&](int base, const uint32_t (&Tw)[6], uint32_t (&dg)[4], uint32_t cand) {
+      const int w0 = base + 16 * lane;      // first window of this lane
+      uint32_t cand_lanes;
       if (two) {
         ++second;
-        if (live && cand != 0u) {
+        if (cand != 0u) {
           or_columns<Q, 2, 0, 0>(Tw, xrep, dg);
-          cand = has_zero_byte(dg[0]) | has_zero_byte(dg[1]) | has_zero_byte(dg[2]) | has_zero_byte(dg[3]);
+          cand = any_zero_byte4(dg);
         }
         cand_lanes = __ballot_sync(0xffffffffu, cand != 0u);
-        if (cand_lanes == 0u) continue;
+        if (cand_lanes == 0u) return;
+      } else {
+        cand_lanes = __ballot_sync(0xffffffffu, cand != 0u);
       }
       // exact zero-byte test: bit 8k+7 of zg[g] is set iff window w0+4g+k
       // equals x (bit 7 of a byte set iff the byte is 0)
@@ -246,7 +252,7 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
             if (out < S) region[out] = rel + static_cast<uint32_t>(w0 + 4 * (p & 7) + (p >> 3));
           }
           t += static_cast<unsigned long long>(__popc(holders));
-          continue;
+          return;
         }
       }
       // general case: the lane's flags in window order (bit i: window w0+i)
@@ -267,6 +273,21 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
         }
       }
       t += __shfl_sync(0xffffffffu, incl, 31);
+        };
+    // hot loop: the first stage only, until some lane of the warp has a
+    // candidate; that step is finished, then the hot loop resumes
+    for (int base = -a.head; base < wins; base += 512) {
+      uint32_t Tw[6], dg[4];
+      uint32_t cand = test(base, Tw, dg);
+      ++steps;
+      while (!__any_sync(0xffffffffu, cand != 0u)) {
+        base += 512;
+        if (base >= wins) break;
+        cand = test(base, Tw, dg);
+        ++steps;
+      }
+      if (base >= wins) break;
+      finish_step(base, Tw, dg, cand);
     }
     if (Q >= 5) {
       if (two && 2 * second > steps) single_left = 16;

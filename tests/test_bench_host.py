@@ -109,3 +109,15 @@ def test_dense_single_pass_rule_matches_the_planner():
     assert not bench.dense_single_pass(hc.SearchOpts(lane_bytes=256, single_pass=1), 4)   # 128 steps per chunk
     assert not bench.dense_single_pass(hc.SearchOpts(lane_bytes=64, tile_steps=64, single_pass=1), 4)  # too big
     assert bench.dense_single_pass(hc.SearchOpts(lane_bytes=16, tile_steps=64, single_pass=1), 4)
+
+
+def test_stored_tuner_table_only_on_gb300():
+    """The committed GB300 tables are the default only on a GB300 and only
+    for the workloads they were measured for; --retune calibrates afresh."""
+    import bench
+    p = bench.stored_tuner_table("sweep", "NVIDIA GB300", False)
+    assert p is not None and p.endswith("profiles/tuner_sweep_gb300.txt")
+    assert bench.stored_tuner_table("skewed", "NVIDIA GB300", False).endswith("tuner_skewed_gb300.txt")
+    assert bench.stored_tuner_table("sweep", "NVIDIA B200", False) is None
+    assert bench.stored_tuner_table("sweep", "NVIDIA GB300", True) is None
+    assert bench.stored_tuner_table("batched", "NVIDIA GB300", False) is None
