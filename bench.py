@@ -315,6 +315,33 @@ def recorded_traffic(family: str, workload: str = "sweep"):
     return ent.get("dram_bytes_per_launch"), ent
 
 
+def recorded_cell_traffic(cell: str, q: int, alpha: int, lane_bytes: int, mode: int,
+                          workload: str = "sweep"):
+    """DRAM bytes of one search of a direct-scan cell (whose reads skip most
+    of the text, so that its bytes are not the text's size) from the
+    committed ncu record (profiles/traffic.json, "direct_cells"), when it was
+    taken on the current kernel sources with the same q, alpha and launch
+    options; else None."""
+    _, rec = recorded_traffic("scan_direct", workload)
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if rec is None and not os.path.exists(path):
+        return None
+    with open(path) as f:
+        allrec = json.load(f)
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, name), "rb") as f:
+            h.update(f.read())
+    if allrec.get("source_sha") != h.hexdigest()[:16]:
+        return None
+    cells = allrec.get("direct_cells", {}) if workload == "sweep" else allrec.get(workload, {}).get("direct_cells", {})
+    ent = cells.get(cell)
+    if not ent or (ent.get("q"), ent.get("alpha"), ent.get("lane_bytes"), ent.get("mode")) != (q, alpha, lane_bytes, mode):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -630,7 +657,22 @@ def run_gpu(args, rank, world, local_rank):
             "lane_bytes": opts.lane_bytes if opts is not None else 0,
             "occ_per_pattern": float(cnt[ci].mean()),
             "hbm_frac": round(alg / cell_s / GB / measured_peaks()[0], 3) if fam != "scan_direct" else None,
+            "hbm_bytes": "text + positions" if fam != "scan_direct" else None,
         }
+    # direct-scan cells: their DRAM bytes from the committed ncu record of
+    # the same launch (a fraction of the text; the positions added)
+    for ci, (s, m) in enumerate(keys):
+        pats, filters, q, alpha, opts = cells[(s, m)]
+        name = f"s{s}_m{m}"
+        if per_cell[name]["kernel"] != "scan_direct":
+            continue
+        dram = recorded_cell_traffic(name, q, alpha, opts.lane_bytes if opts is not None else 0,
+                                     opts.mode if opts is not None else 0, args.workload)
+        if dram is not None:
+            occ = float(cnt[ci].sum())
+            byts = (dram * args.patterns + pos_bytes * occ) * args.steps
+            per_cell[name]["hbm_frac"] = round(byts / (cell_ms[ci] / 1e3) / GB / measured_peaks()[0], 3)
+            per_cell[name]["hbm_bytes"] = "ncu DRAM bytes of the scan (profiles/traffic.json) + positions"
     dominant = max(kernel_times, key=lambda k: kernel_times[k][0])
     dom_ms, dom_launches = kernel_times[dominant]
     achieved = fam_bytes.get(dominant, 0.0) * args.steps / (dom_ms / 1e3) / GB if dom_ms else 0.0

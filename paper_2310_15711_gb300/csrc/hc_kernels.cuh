@@ -412,10 +412,11 @@ constexpr int kFirstTests = 4;
 // first unlinked q-gram -- the same break point the sequential walk reaches.
 // A fully read window is then checked against H_v and verified by the warp.
 // All 32 lanes of a warp must call this together (an empty range is fine).
-template <int Q, bool STAGED, int MODE>
+template <int Q, bool STAGED, int MODE, int FT = 1>
 __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int lo, int hi,
                                             const SearchArgs& a, const uint32_t* Fs,
-                                            const uint8_t* xv, const Sink& sink) {
+                                            const uint8_t* xv, const Sink& sink,
+                                            int* tests = nullptr, int* hits = nullptr) {
   const int lane = threadIdx.x & 31;
   const int m = a.m;
   const uint32_t hv = a.hv;
@@ -428,35 +429,40 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
   bool deep = false;               // window at e waits for the warp
   int dj = 0;                      // walk position reached
   uint32_t dz = 0;                 // F word of the q-gram ending at dj
+  int n_tests = 0, n_hits = 0;      // first tests made and passed (FT > 1 only)
   while (true) {
     while (!deep && e < e_end) {
-      // first tests of the next kFirstTests windows of the miss sequence e,
-      // e + shift, ... at once (independent loads, one branch per run): each
+      // first tests of the next FT windows of the miss sequence e, e +
+      // shift, ... at once (independent loads, one branch per run): each
       // window whose end q-gram hits an empty word is shifted past, as the
       // sequential loop does; the first window that hits a non-empty word
       // goes on to the back-walk.  Windows past the segment take no part
       // (their test reads window e's q-gram and is discarded).
       uint32_t v = 0, z = 0;
       {
-        uint32_t vu[kFirstTests], zu[kFirstTests];
+        uint32_t vu[FT], zu[FT];
 #pragma unroll
-        for (int u = 0; u < kFirstTests; ++u) {
+        for (int u = 0; u < FT; ++u) {
           const int ek = e + u * shift;
           const bool in = u == 0 || ek < e_end;
           vu[u] = qgram_hash_k<Q, STAGED>(base, head + (in ? ek : e) - Q + 1, a, hk);
           zu[u] = in ? Fs[vu[u]] : 0u;
         }
-        int k = kFirstTests;
+        int k = FT;
 #pragma unroll
-        for (int u = kFirstTests - 1; u >= 0; --u) {
+        for (int u = FT - 1; u >= 0; --u) {
           if (zu[u] != 0u) {
             k = u;
             v = vu[u];
             z = zu[u];
           }
         }
-        if (k == kFirstTests) {
-          e += kFirstTests * shift;
+        if constexpr (FT > 1) {
+          n_tests += k == FT ? FT : k + 1;
+          n_hits += k < FT ? 1 : 0;
+        }
+        if (k == FT) {
+          e += FT * shift;
           continue;
         }
         e += k * shift;
@@ -512,6 +518,8 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
       }
     }
   }
+  if (tests != nullptr) *tests = n_tests;
+  if (hits != nullptr) *hits = n_hits;
   return cnt;
 }
 
@@ -592,6 +600,8 @@ __device__ __forceinline__ void warp_stream(const SearchArgs& a, unsigned long l
 
   const unsigned long long S = a.region_entries;
   uint32_t* region = a.region + w_id * S;
+  bool batch_first = true;                // first tests four at a time (warp-uniform)
+  int probe_in = 0;                       // chunks until the batched form is tried again
   unsigned long long T = 0;               // occurrences so far in this range
   unsigned long long overflow = kNoOverflow;
   Sink sink{};
@@ -640,7 +650,19 @@ __device__ __forceinline__ void warp_stream(const SearchArgs& a, unsigned long l
     }
     const int lo = lane * a.L;
     const int hi = max(lo, min(lo + a.L, wins));
-    const int cnt = scan_segment<Q, STAGED, kCount>(base, head, lo, hi, a, Fs, xv, sink);
+    // first tests four at a time while few of them pass (one window in 16
+    // or fewer over the warp's last chunk), one at a time otherwise: where
+    // many pass, the batch's later tests are wasted and its lanes diverge
+    int tests = 0, hits = 0;
+    const int cnt = batch_first
+                        ? scan_segment<Q, STAGED, kCount, kFirstTests>(base, head, lo, hi, a, Fs, xv, sink, &tests, &hits)
+                        : scan_segment<Q, STAGED, kCount, 1>(base, head, lo, hi, a, Fs, xv, sink);
+    if (batch_first) {
+      const int wt = __reduce_add_sync(0xffffffffu, tests), wh = __reduce_add_sync(0xffffffffu, hits);
+      if (wh * 16 > wt) { batch_first = false; probe_in = 32; }
+    } else if (--probe_in == 0) {
+      batch_first = true;  // look again now and then
+    }
 
     if (__any_sync(0xffffffffu, cnt != 0)) {
       const uint32_t incl = warp_incl_scan_u32(static_cast<uint32_t>(cnt));

@@ -56,7 +56,7 @@ __device__ unsigned int g_status;
 // memory.  Occurrences go, in text order, to the warp's spill region; the
 // total to cta_total[w].  No CTA-wide barrier in the loop.
 template <int Q, bool STAGED>
-__global__ void __launch_bounds__(kThreads, STAGED ? 4 : 5) hc_scan_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) hc_scan_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
   pdl_launch_dependents();  // the emit kernel may be scheduled; it waits for this grid
@@ -274,20 +274,19 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
       }
       t += __shfl_sync(0xffffffffu, incl, 31);
         };
-    // hot loop: the first stage only, until some lane of the warp has a
-    // candidate; that step is finished, then the hot loop resumes
-    for (int base = -a.head; base < wins; base += 512) {
-      uint32_t Tw[6], dg[4];
-      uint32_t cand = test(base, Tw, dg);
-      ++steps;
-      while (!__any_sync(0xffffffffu, cand != 0u)) {
-        base += 512;
-        if (base >= wins) break;
-        cand = test(base, Tw, dg);
-        ++steps;
+    // hot loop: the first stage of two steps at once (independent loads,
+    // one vote for both); a step in which some lane has a candidate is
+    // finished apart.  A step past the chunk's end tests nothing (all its
+    // lanes are past the end).
+    for (int base = -a.head; base < wins; base += 1024) {
+      uint32_t Tw0[6], dg0[4], Tw1[6], dg1[4];
+      const uint32_t c0 = test(base, Tw0, dg0);
+      const uint32_t c1 = test(base + 512, Tw1, dg1);
+      steps += 2;
+      if (__any_sync(0xffffffffu, (c0 | c1) != 0u)) {
+        if (__any_sync(0xffffffffu, c0 != 0u)) finish_step(base, Tw0, dg0, c0);
+        if (__any_sync(0xffffffffu, c1 != 0u)) finish_step(base + 512, Tw1, dg1, c1);
       }
-      if (base >= wins) break;
-      finish_step(base, Tw, dg, cand);
     }
     if (Q >= 5) {
       if (two && 2 * second > steps) single_left = 16;

@@ -24,7 +24,8 @@ namespace hc {
 
 constexpr uint32_t kTunerMagic = 0x48435455u;  // "HCTU"
 constexpr uint64_t kScreenBytes = 8ull << 20;  // text per screening run
-constexpr size_t kFinalists = 4;                // candidates timed on the whole text
+constexpr size_t kFinalists = 8;                // candidates timed on the whole text
+constexpr int kTunePatterns = 5;                 // patterns the finalists are timed on
 
 struct Tuner {
   uint32_t magic = kTunerMagic;
@@ -295,19 +296,36 @@ int time_candidate_single(Scratch& sc, int dev, const std::vector<uint8_t>& xh, 
 
 int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n, int sigma, uint64_t m,
                    uint64_t seed, int path, cudaStream_t stream, cudaEvent_t e0, cudaEvent_t e1) {
-  // the pattern: m bytes of the text at a seeded offset
-  const uint64_t off = (seed * 0x9E3779B97F4A7C15ull ^ m * 0xBF58476D1CE4E5B9ull) % (n - m + 1);
-  const uint8_t* x = y + off;
-  std::vector<uint8_t> xh(m);
-  if (path == HC_TUNE_SINGLE) {
-    cudaError_t e = cudaMemcpy(xh.data(), x, m, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(calibration pattern)");
+  // the patterns: m bytes of the text at seeded offsets (the screening uses
+  // the first; the finalists are timed on all of them, so that one pattern's
+  // particular q-grams do not decide the cell)
+  const uint8_t* xs[kTunePatterns];
+  std::vector<uint8_t> xh[kTunePatterns];
+  for (int k = 0; k < kTunePatterns; ++k) {
+    const uint64_t off = ((seed + 7919ull * k) * 0x9E3779B97F4A7C15ull ^ m * 0xBF58476D1CE4E5B9ull) % (n - m + 1);
+    xs[k] = y + off;
+    xh[k].resize(m);
+    if (path == HC_TUNE_SINGLE) {
+      cudaError_t e = cudaMemcpy(xh[k].data(), xs[k], m, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(calibration pattern)");
+    }
   }
-  // timed on the first nn bytes of the text: reps runs (after an untimed one when warm)
-  auto time_it = [&](const QueryParams& p, uint64_t nn, int reps, bool warm, double* s, int* L, int* mode) {
-    return path == HC_TUNE_SINGLE
-               ? time_candidate_single(sc, dev, xh, y, nn, p, reps, warm, stream, e0, e1, s, L, mode)
-               : time_candidate(sc, dev, x, m, y, nn, p, reps, warm, stream, e0, e1, s, L, mode);
+  // timed on the first nn bytes of the text with `npat` patterns: reps runs
+  // each (after an untimed one when warm), the patterns' best times summed
+  auto time_it = [&](const QueryParams& p, uint64_t nn, int reps, bool warm, double* s, int* L, int* mode,
+                     int npat = kTunePatterns) -> int {
+    double total = 0;
+    for (int k = 0; k < npat; ++k) {
+      double sk = INFINITY;
+      const int rc = path == HC_TUNE_SINGLE
+                         ? time_candidate_single(sc, dev, xh[k], y, nn, p, reps, warm, stream, e0, e1, &sk, L, mode)
+                         : time_candidate(sc, dev, xs[k], m, y, nn, p, reps, warm, stream, e0, e1, &sk, L, mode);
+      if (rc != HC_OK) return rc;
+      total += sk;
+      if (!std::isfinite(sk)) break;
+    }
+    *s = total;
+    return HC_OK;
   };
   // screening: every (q, alpha) once on a prefix of the text (a poor
   // candidate can be orders of magnitude slower than a good one: every
@@ -326,7 +344,7 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
       p.alpha = alpha;
       double s = INFINITY;
       int L = 0, mode = 0;
-      int rc = time_it(p, n_screen, 1, false, &s, &L, &mode);
+      int rc = time_it(p, n_screen, 1, false, &s, &L, &mode, 1);
       if (rc != HC_OK) return rc;
       if (std::isfinite(s)) screened.push_back({s, p});
     }
@@ -373,7 +391,7 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
   c.alpha = bp.alpha;
   c.lane_bytes = best_L;
   c.mode = best_mode;
-  c.gbps = static_cast<double>(n) / best / 1e9;
+  c.gbps = static_cast<double>(n) * kTunePatterns / best / 1e9;
   std::lock_guard<std::mutex> lock(t->mu);
   put_cell(t, c);
   return HC_OK;

@@ -121,3 +121,31 @@ def test_stored_tuner_table_only_on_gb300():
     assert bench.stored_tuner_table("sweep", "NVIDIA B200", False) is None
     assert bench.stored_tuner_table("sweep", "NVIDIA GB300", True) is None
     assert bench.stored_tuner_table("batched", "NVIDIA GB300", False) is None
+
+
+def test_direct_cell_traffic_needs_the_same_launch(tmp_path, monkeypatch):
+    """A direct-scan cell's recorded DRAM bytes are used only for the same
+    q, alpha, lane_bytes and mode, on the kernel sources they were taken on."""
+    import hashlib
+    import json
+    import os
+    root = tmp_path
+    (root / "profiles").mkdir()
+    for name in bench.KERNEL_SOURCES:
+        os.makedirs(root / os.path.dirname(name), exist_ok=True)
+        (root / name).write_bytes(b"src " + name.encode())
+    h = hashlib.sha256()
+    for name in bench.KERNEL_SOURCES:
+        h.update((root / name).read_bytes())
+    rec = {"source_sha": h.hexdigest()[:16],
+           "direct_cells": {"s4_m1024": {"q": 8, "alpha": 12, "lane_bytes": 2036, "mode": 2,
+                                         "dram_bytes_per_launch": 37_000_000}}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.recorded_cell_traffic("s4_m1024", 8, 12, 2036, 2) == 37_000_000
+    assert bench.recorded_cell_traffic("s4_m1024", 8, 11, 2036, 2) is None   # other alpha
+    assert bench.recorded_cell_traffic("s4_m512", 8, 12, 2036, 2) is None    # no record
+    assert bench.recorded_cell_traffic("s4_m1024", 8, 12, 2036, 2, "skewed") is None
+    rec["source_sha"] = "1" * 16
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.recorded_cell_traffic("s4_m1024", 8, 12, 2036, 2) is None
