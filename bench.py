@@ -465,7 +465,8 @@ def run_gpu(args, rank, world, local_rank):
             if kind == "tuned":
                 e = tuner.lookup(tune_sigma[s], m)
                 q, alpha = e["q"], e["alpha"]
-                opts = hc.SearchOpts(lane_bytes=e["lane_bytes"], mode=e["mode"], pos32=pos32)
+                opts = hc.SearchOpts(lane_bytes=e["lane_bytes"], mode=e["mode"], pos32=pos32,
+                                     sentinel=e.get("sentinel", 0))
             else:
                 q, alpha = hi.paper_q_alpha(s, m)
                 opts = hc.SearchOpts(pos32=pos32)

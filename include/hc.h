@@ -168,6 +168,15 @@ typedef struct hc_search_opts {
     int tile_steps;         /* single pass: window steps of 512 per tile
                                (1..64, rounded up to whole chunks);
                                0 = automatic */
+    int sentinel;           /* staged mode: 1 -- the GPU form of SHC's
+                               sentinel (Sec. 3.4, third optimisation): the
+                               staging buffers are padded so that a lane's
+                               loop of first tests may read past its run of
+                               window starts, and the window position is
+                               tested once per round of four first tests and
+                               once per test that passes, instead of for
+                               every window; 0 -- HC's position test per
+                               window */
 } hc_search_opts;
 
 /* hc_search_ex: hc_search_async with explicit launch options (opts may be
@@ -234,7 +243,8 @@ typedef struct hc_batch hc_batch;
 typedef struct hc_tune_entry {
     int sigma;
     int q, alpha, lane_bytes, mode;
-    int reserved;
+    int sentinel;           /* 1: the staged mode's sentinel form
+                               (hc_search_opts.sentinel) */
     uint64_t m;
     double gbps;
 } hc_tune_entry;

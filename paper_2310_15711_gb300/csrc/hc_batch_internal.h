@@ -39,6 +39,7 @@ struct BatchLayout {
 // per lane (0 = automatic) and scan mode (HC_MODE_AUTO, _STAGED, _DIRECT).
 struct QueryParams {
   int q = 0, alpha = 0, lane_bytes = 0, mode = 0;
+  int sentinel = 0;  // single searches in the staged mode: the sentinel form
 };
 
 // Queries are grouped by the number of CTAs per SM their own shared-memory

@@ -131,6 +131,7 @@ struct SearchPlan {
   unsigned long long records = 0;  // spill records: one per CTA (one per warp when dense)
   unsigned long long emit_group = 0, emit_ctas = 0;  // emit kernel: records per CTA group, CTAs
   bool spec = false;              // warp-speculative HC (staged/direct kinds)
+  bool unchecked = false;         // staged: padded buffers, no position test per first test
   bool pos32 = false;             // positions written as uint32
   size_t ws_bytes = 0;            // workspace bytes (device), no zeroing needed
   // single-pass dense form: an init kernel zeroes the tile ticket and the

@@ -67,6 +67,7 @@ struct SearchArgs {
   int stages;                // staging buffers per CTA (2..kMaxStages)
   unsigned long long records;     // spill records (one per warp)
   int spec;                       // 1: warp-speculative HC per chunk (rare first-test hits)
+  int unchecked;                  // 1: staged, padded buffers: no position test per first test
   unsigned long long emit_group;  // records served by one emit CTA group
   // h as at most two byte-dot-products (see qgram_hash): bytes [0, g0) with
   // weights w0, bytes [g0, q) with weights w1, scaled by 2^(s*g0)
@@ -412,7 +413,7 @@ constexpr int kFirstTests = 4;
 // first unlinked q-gram -- the same break point the sequential walk reaches.
 // A fully read window is then checked against H_v and verified by the warp.
 // All 32 lanes of a warp must call this together (an empty range is fine).
-template <int Q, bool STAGED, int MODE, int FT = 1>
+template <int Q, bool STAGED, int MODE, int FT = 1, bool UNCHECKED = false>
 __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int lo, int hi,
                                             const SearchArgs& a, const uint32_t* Fs,
                                             const uint8_t* xv, const Sink& sink,
@@ -444,7 +445,9 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
 #pragma unroll
         for (int u = 0; u < FT; ++u) {
           const int ek = e + u * shift;
-          const bool in = u == 0 || ek < e_end;
+          // with UNCHECKED (padded buffers) windows past the segment are
+          // tested too; a hit there ends the segment below
+          const bool in = UNCHECKED || u == 0 || ek < e_end;
           vu[u] = qgram_hash_k<Q, STAGED>(base, head + (in ? ek : e) - Q + 1, a, hk);
           zu[u] = in ? Fs[vu[u]] : 0u;
         }
@@ -466,6 +469,9 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
           continue;
         }
         e += k * shift;
+        if constexpr (UNCHECKED) {
+          if (e >= e_end) continue;  // the first hit lies past the segment: done
+        }
       }
       // back-walk over the q-grams to the left, each linked to its right one
       int j = e;
@@ -654,9 +660,13 @@ __device__ __forceinline__ void warp_stream(const SearchArgs& a, unsigned long l
     // or fewer over the warp's last chunk), one at a time otherwise: where
     // many pass, the batch's later tests are wasted and its lanes diverge
     int tests = 0, hits = 0;
-    const int cnt = batch_first
-                        ? scan_segment<Q, STAGED, kCount, kFirstTests>(base, head, lo, hi, a, Fs, xv, sink, &tests, &hits)
-                        : scan_segment<Q, STAGED, kCount, 1>(base, head, lo, hi, a, Fs, xv, sink);
+    int cnt;
+    if (!batch_first)
+      cnt = scan_segment<Q, STAGED, kCount, 1>(base, head, lo, hi, a, Fs, xv, sink);
+    else if (STAGED && a.unchecked)
+      cnt = scan_segment<Q, STAGED, kCount, kFirstTests, STAGED>(base, head, lo, hi, a, Fs, xv, sink, &tests, &hits);
+    else
+      cnt = scan_segment<Q, STAGED, kCount, kFirstTests>(base, head, lo, hi, a, Fs, xv, sink, &tests, &hits);
     if (batch_first) {
       const int wt = __reduce_add_sync(0xffffffffu, tests), wh = __reduce_add_sync(0xffffffffu, hits);
       if (wh * 16 > wt) { batch_first = false; probe_in = 32; }

@@ -536,6 +536,16 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
     }
   }
   p.kind = kind;
+  const int sentinel = o ? o->sentinel : 0;
+  if (sentinel < 0 || sentinel > 1) return set_error(HC_ERR_ARG, "hc_search: sentinel must be 0 or 1");
+  if (sentinel == 1 && kind != HC_MODE_STAGED)
+    return set_error(HC_ERR_ARG, "hc_search: the sentinel form applies to the staged mode only");
+  if (kind == HC_MODE_STAGED && sentinel == 1) {
+    // a lane's round of four first tests may reach three shifts past its
+    // last window end (and the q-gram's three words 12 bytes further)
+    p.stage_bytes += static_cast<uint32_t>((3 * shift + 16 + 15) & ~15);
+    p.unchecked = true;
+  }
   if (kind == HC_MODE_STAGED) {
     p.scan = scan_kernel_for_q<true>(f->q);
     p.smem_scan = fbytes + p.x_smem + slot_bytes + size_t(kWarps) * stages * p.stage_bytes;
@@ -685,6 +695,7 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
   a.stages = p.stages;
   a.records = p.records;
   a.spec = p.spec ? 1 : 0;
+  a.unchecked = p.unchecked ? 1 : 0;
   a.pos32 = p.pos32 ? 1 : 0;
   a.emit_group = p.emit_group;
   // byte groups of h: the longest prefix whose weights 2^(s*k) fit in a byte

@@ -250,6 +250,7 @@ int time_candidate_single(Scratch& sc, int dev, const std::vector<uint8_t>& xh, 
   o.struct_size = sizeof o;
   o.lane_bytes = p.lane_bytes;
   o.mode = p.mode;
+  o.sentinel = p.sentinel;
   SearchPlan sp;
   if (plan_search(f, n, 0, &o, dev, &sp) != HC_OK) {
     clear_error();
@@ -384,6 +385,23 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
         best_mode = mr;
       }
     }
+  // the sentinel form of the staged scan (single searches): kept where it
+  // is faster
+  int best_sentinel = 0;
+  if (path == HC_TUNE_SINGLE && best_mode == HC_MODE_STAGED) {
+    QueryParams p = bp;
+    p.lane_bytes = best_L;
+    p.mode = HC_MODE_STAGED;
+    p.sentinel = 1;
+    double s = INFINITY;
+    int Lr = 0, mr = 0;
+    int rc = time_it(p, n, 3, true, &s, &Lr, &mr);
+    if (rc != HC_OK) return rc;
+    if (s < best && mr == HC_MODE_STAGED) {
+      best = s;
+      best_sentinel = 1;
+    }
+  }
   hc_tune_entry c{};
   c.sigma = sigma;
   c.m = m;
@@ -391,6 +409,7 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
   c.alpha = bp.alpha;
   c.lane_bytes = best_L;
   c.mode = best_mode;
+  c.sentinel = best_sentinel;
   c.gbps = static_cast<double>(n) * kTunePatterns / best / 1e9;
   std::lock_guard<std::mutex> lock(t->mu);
   put_cell(t, c);
@@ -433,6 +452,7 @@ QueryParams tuner_lookup(const Tuner* t, double sigma, uint64_t m) {
   p.alpha = best.alpha;
   p.lane_bytes = best.lane_bytes;
   p.mode = best.mode;
+  p.sentinel = best.sentinel;
   if (best.m != m) {
     // launch options measured for another length: keep them only where they
     // still fit (the staged form's buffers grow with m; the dense form needs
@@ -441,6 +461,7 @@ QueryParams tuner_lookup(const Tuner* t, double sigma, uint64_t m) {
         (p.mode == HC_MODE_DENSE && static_cast<uint64_t>(p.q) != m)) {
       p.mode = HC_MODE_AUTO;
       p.lane_bytes = 0;
+      p.sentinel = 0;
     }
   }
   return p;
@@ -533,6 +554,7 @@ int hc_tuner_lookup(const hc_tuner* tp, double sigma, uint64_t m, hc_tune_entry*
   out->alpha = p.alpha;
   out->lane_bytes = p.lane_bytes;
   out->mode = p.mode;
+  out->sentinel = p.sentinel;
   return HC_OK;
 }
 
@@ -560,10 +582,10 @@ int hc_tuner_save(const hc_tuner* tp, const char* path) {
   FILE* f = std::fopen(path, "w");
   if (f == nullptr) return set_error(HC_ERR_STATE, std::string("hc_tuner_save: cannot open ") + path);
   std::lock_guard<std::mutex> lock(t->mu);
-  std::fprintf(f, "# sigma m q alpha lane_bytes mode gbps\n");
+  std::fprintf(f, "# sigma m q alpha lane_bytes mode gbps sentinel\n");
   for (const auto& c : t->cells)
-    std::fprintf(f, "%d %llu %d %d %d %d %.3f\n", c.sigma, static_cast<unsigned long long>(c.m), c.q, c.alpha,
-                 c.lane_bytes, c.mode, c.gbps);
+    std::fprintf(f, "%d %llu %d %d %d %d %.3f %d\n", c.sigma, static_cast<unsigned long long>(c.m), c.q, c.alpha,
+                 c.lane_bytes, c.mode, c.gbps, c.sentinel);
   const bool ok = std::fclose(f) == 0;
   return ok ? HC_OK : set_error(HC_ERR_STATE, "hc_tuner_save: write failed");
 }
@@ -584,8 +606,10 @@ int hc_tuner_load(hc_tuner* tp, const char* path) {
     if (*s == '#' || *s == '\n' || *s == '\0') continue;
     hc_tune_entry c{};
     unsigned long long m = 0;
-    if (std::sscanf(s, "%d %llu %d %d %d %d %lf", &c.sigma, &m, &c.q, &c.alpha, &c.lane_bytes, &c.mode,
-                    &c.gbps) != 7 ||
+    // the last column (sentinel form) is optional: 0 when absent
+    const int got_fields = std::sscanf(s, "%d %llu %d %d %d %d %lf %d", &c.sigma, &m, &c.q, &c.alpha,
+                                       &c.lane_bytes, &c.mode, &c.gbps, &c.sentinel);
+    if (got_fields < 7 || c.sentinel < 0 || c.sentinel > 1 || (c.sentinel == 1 && c.mode != HC_MODE_STAGED) ||
         c.sigma < 1 || m < 1 || c.q < 1 || c.q > kMaxQ || static_cast<unsigned long long>(c.q) > m ||
         c.alpha < 1 || c.alpha > kMaxAlpha || c.lane_bytes < 0 || c.lane_bytes > 4096 ||
         (c.mode != HC_MODE_AUTO && c.mode != HC_MODE_STAGED && c.mode != HC_MODE_DIRECT &&

@@ -441,7 +441,8 @@ def test_search_opts_rejected_when_out_of_range():
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     for bad in (dict(lane_bytes=5000), dict(stages=5), dict(stages=1), dict(mode=3),
                 dict(mode=7), dict(single_pass=2), dict(single_pass=-2), dict(tile_steps=65),
-                dict(tile_steps=-1), dict(mode=1, single_pass=1)):
+                dict(tile_steps=-1), dict(mode=1, single_pass=1), dict(sentinel=2),
+                dict(mode=2, sentinel=1), dict(mode=3, sentinel=1)):
         with pytest.raises(hc.HCError) as ei:
             hc.hc_search_ex(f, y_dev, None, cnt, hc.SearchOpts(**bad))
         assert ei.value.code == hc.HC_ERR_ARG
@@ -524,4 +525,39 @@ def test_full_size_in_the_timed_launch_configuration():
             assert np.array_equal(got[1:1 + want.size].view(np.uint32).astype(np.uint64), want), (sigma, m)
             assert got[0] == -7 and (got[1 + want.size:] == -7).all(), (sigma, m)
         del g
+        f.free()
+
+
+@pytest.mark.parametrize("lane_bytes", [0, 4, 37, 188])
+def test_sentinel_form_of_the_staged_scan(lane_bytes):
+    """The sentinel form (SHC's idea on the GPU: the staging buffers are
+    padded so that a lane's first tests run past its window starts with no
+    position test per window) gives exactly the oracle's HC and SHC results
+    for every q, patterns long and short, periodic and random texts, every
+    16-byte offset of the text."""
+    hc = _hc()
+    rng = np.random.default_rng(900 + lane_bytes)
+    for trial in range(36):
+        sigma = int(rng.choice([1, 2, 4, 20, 95]))
+        m = int(rng.choice([2, 3, 5, 9, 16, 33, 100, 180]))
+        q = int(rng.integers(1, min(m, 8) + 1))
+        alpha = int(rng.choice([4, 8, 11, 12, 15]))
+        x, y = _case(rng, sigma, int(rng.integers(1, 300_000)), m, plant=int(rng.integers(0, 40)))
+        want = oracle.hc_search(x, y, q, alpha)
+        assert np.array_equal(want, oracle.shc_search(x, y, q, alpha))
+        y_dev, keep = _upload(y, offset=trial % 16)
+        f = hc.hc_preprocess(x, q, alpha)
+        for cap in (want.size + 2, max(want.size // 2, 1)):
+            pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            try:
+                hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(mode=1, sentinel=1, lane_bytes=lane_bytes))
+            except hc.HCError as ex:      # staging buffers too large for this m, alpha
+                assert ex.code == hc.HC_ERR_ARG
+                break
+            torch.cuda.synchronize()
+            hc.hc_check_status()
+            assert int(cnt.item()) == want.size, (sigma, m, q, alpha)
+            k = min(cap, want.size)
+            assert np.array_equal(pos[:k].cpu().numpy().view(np.uint64), want[:k]), (sigma, m, q, alpha, cap)
         f.free()

@@ -104,9 +104,28 @@ def test_save_load_round_trip_and_replace(hc, tmp_path):
     t2.free()
 
 
+def test_sentinel_column_round_trips(hc, tmp_path):
+    """The optional last column marks a staged cell measured fastest in the
+    sentinel form; lookups return it, files without it read 0."""
+    p = str(tmp_path / "s.txt")
+    _write(p, ["20 32 6 12 124 1 5.5 1", "4 16 6 12 68 1 4.5", "95 2 2 12 16 3 5 0"])
+    t = hc.HCTuner()
+    t.load(p)
+    assert t.lookup(20, 32)["sentinel"] == 1
+    assert t.lookup(4, 16)["sentinel"] == 0
+    q = str(tmp_path / "s2.txt")
+    t.save(q)
+    t2 = hc.HCTuner()
+    t2.load(q)
+    assert t2.entries() == t.entries()
+    assert t2.lookup(20, 32)["sentinel"] == 1
+    t.free()
+    t2.free()
+
+
 @pytest.mark.parametrize("bad", ["4 8 9 12 0 0 1", "4 8 4 16 0 0 1", "4 8 4 12 0 7 1", "4 8 4 12 0 3 1",
                                  "4 2 3 12 0 0 1", "0 8 4 12 0 0 1", "4 8 4 12 0 0",
-                                 "4 8 4 12 5000 0 1", "garbage"])
+                                 "4 8 4 12 5000 0 1", "garbage", "4 8 4 12 0 2 1 1", "4 8 4 12 0 1 1 2"])
 def test_malformed_lines_rejected(hc, tmp_path, bad):
     p = str(tmp_path / "bad.txt")
     _write(p, ["4 16 6 12 0 0 1", bad])
