@@ -102,6 +102,8 @@ def parse_args():
     ap.add_argument("--skew-n", type=int, default=1 << 30, help="skewed text length")
     ap.add_argument("--served-rates", type=int, nargs="+", default=list(SERVED_RATES_DEFAULT))
     ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-reps", type=int, default=3,
+                    help="repetitions of each offered load per server (order alternating; latencies pooled)")
     ap.add_argument("--served-backlog", type=int, default=50000,
                     help="requests submitted at once for the saturation measurement")
     ap.add_argument("--batch-queries", type=int, default=4096)
@@ -257,7 +259,8 @@ def scan_family(m: int, q: int, mode: int = 0) -> str:
     return "scan_staged"
 
 
-TUNER_TABLES = {"sweep": "profiles/tuner_sweep_gb300.txt", "skewed": "profiles/tuner_skewed_gb300.txt"}
+TUNER_TABLES = {"sweep": "profiles/tuner_sweep_gb300.txt", "skewed": "profiles/tuner_skewed_gb300.txt",
+                "batched": "profiles/tuner_batched_gb300.txt"}
 
 
 def stored_tuner_table(workload: str, device_name: str, retune: bool):
@@ -466,7 +469,7 @@ def run_gpu(args, rank, world, local_rank):
                 e = tuner.lookup(tune_sigma[s], m)
                 q, alpha = e["q"], e["alpha"]
                 opts = hc.SearchOpts(lane_bytes=e["lane_bytes"], mode=e["mode"], pos32=pos32,
-                                     sentinel=e.get("sentinel", 0))
+                                     sentinel=e.get("sentinel", 0), bitmap=e.get("bitmap", 0))
             else:
                 q, alpha = hi.paper_q_alpha(s, m)
                 opts = hc.SearchOpts(pos32=pos32)
@@ -630,7 +633,9 @@ def run_gpu(args, rank, world, local_rank):
 
     # algorithmic bytes per kernel family (per step): the scan kernels read
     # the text once and spill 4 bytes per occurrence; the emit kernel reads
-    # those 4 and writes the position (4 or 8 bytes)
+    # those 4 and writes the position (4 or 8 bytes).  In the dense scan's
+    # bitmap form the scan writes one bit per window instead and the emit
+    # reads those bits back.
     cnt = counts.cpu().numpy()
     fam_bytes = {}
     per_cell = {}
@@ -642,6 +647,10 @@ def run_gpu(args, rank, world, local_rank):
         if fam == "scan_dense" and dense_single_pass(opts, m):
             # one kernel reads the text and writes each position once
             fam_bytes[fam] = fam_bytes.get(fam, 0.0) + n * args.patterns + pos_bytes * occ
+        elif fam == "scan_dense" and getattr(opts, "bitmap", 0) == 1:
+            bits = (n - m + 1) / 8.0 * args.patterns
+            fam_bytes[fam] = fam_bytes.get(fam, 0.0) + n * args.patterns + bits
+            fam_bytes["emit"] = fam_bytes.get("emit", 0.0) + bits + pos_bytes * occ
         else:
             fam_bytes[fam] = fam_bytes.get(fam, 0.0) + n * args.patterns + 4 * occ
             fam_bytes["emit"] = fam_bytes.get("emit", 0.0) + (4 + pos_bytes) * occ
@@ -649,13 +658,15 @@ def run_gpu(args, rank, world, local_rank):
         # algorithmic DRAM bytes of the cell's searches: the text once (every
         # byte is read when the whole text is staged; direct-mode cells read
         # less) and each position written once.  The spill region's write and
-        # read (8 bytes per occurrence) are this implementation's overhead and
-        # are not counted.
+        # read (8 bytes per occurrence), or the bitmap form's bits, are this
+        # implementation's overhead and are not counted.
         alg = (n * args.patterns + pos_bytes * occ) * args.steps
         per_cell[f"s{s}_m{m}"] = {
             "GBps": round(n * args.patterns * args.steps / cell_s / GB, 1),
             "kernel": fam, "q": q, "alpha": alpha,
             "lane_bytes": opts.lane_bytes if opts is not None else 0,
+            "form": ("bitmap" if getattr(opts, "bitmap", 0) == 1 else
+                     "sentinel" if getattr(opts, "sentinel", 0) == 1 else "plain"),
             "occ_per_pattern": float(cnt[ci].mean()),
             "hbm_frac": round(alg / cell_s / GB / measured_peaks()[0], 3) if fam != "scan_direct" else None,
             "hbm_bytes": "text + positions" if fam != "scan_direct" else None,
@@ -792,10 +803,23 @@ def run_batched(args, rank, world, local_rank):
             out.append(d)
         return out
 
+    # the batched tuner's table: the stored GB300 one (the calibration's
+    # choices vary from run to run, and with them the batch's rate), else
+    # calibrated here (saved to --tuner-table when given)
     tuner = hc.HCTuner()
     t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        tuner.calibrate([4, 20], BATCH_TUNE_MS, text_bytes=args.tune_text_bytes, seed=11, stream=stream)
+    table = getattr(args, "tuner_table", "") or stored_tuner_table(
+        "batched", torch.cuda.get_device_name(dev), getattr(args, "retune", False))
+    if table and os.path.exists(table):
+        tuner.load(table)
+        tuner_source = table
+    else:
+        with torch.cuda.stream(stream):
+            tuner.calibrate([4, 20], BATCH_TUNE_MS, text_bytes=args.tune_text_bytes, seed=11, stream=stream)
+        stream.synchronize()
+        if getattr(args, "tuner_table", ""):
+            tuner.save(args.tuner_table)
+        tuner_source = "calibrated in this run"
     tune_s = time.perf_counter() - t0
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
@@ -881,6 +905,7 @@ def run_batched(args, rank, world, local_rank):
         "config": {"workload": "batched HC", "queries": len(qrs), "text_bytes": int(text_bytes),
                    "n": "log-uniform 4 KiB .. 64 MiB", "m": "log-uniform 4 .. 512",
                    "sigma": "{4, 20}", "q_alpha": "autotuned per (measured sigma, m)",
+                   "tuner_table": tuner_source,
                    "l2": "27 GB of texts, far larger than L2; no flush"},
         "queries_per_s": round(len(qrs) / t_batch, 1),
         "paper_params_GBps": round(text_bytes / t_paper / GB, 2),
@@ -922,10 +947,12 @@ def run_served(args, rank, world, local_rank):
     50k requests/s (m log-uniform 2 to 1024, each pattern copied from its
     text), replayed natively into an hc_server (continuous batching, 32 GiB
     admission, tuned parameters) and into a plain server (one search launch
-    per request, same parameters).  Reports per load p50/p99 latency (from
-    the scheduled arrival to the result on the host), achieved requests/s
-    and aggregate text GB/s (sum of n over the span from first arrival to
-    last result), and whether every count matches between the two."""
+    per request, same parameters), each load repeated --served-reps times
+    per server in alternating order.  Reports per load p50/p99 latency over
+    the pooled repetitions (from the scheduled arrival to the result on the
+    host) and each repetition's p99, achieved requests/s and aggregate text
+    GB/s (sum of n over the spans from first arrival to last result), and
+    whether every count matches between the two."""
     import torch
     import paper_2310_15711_gb300 as hc
 
@@ -944,49 +971,80 @@ def run_served(args, rank, world, local_rank):
     loads = []
     sampler = ClockSampler(local_rank, interval_ms=max(args.clock_ms, 1), enabled=args.clock_ms > 0)
     sampler.start()
+    # both servers live side by side (texts resident in each); each load runs
+    # `reps` times per server, the order alternating, and the latencies of
+    # all repetitions are pooled, so that a slow moment of the host does not
+    # fall on one server only
+    servers = {}
+    for plain in (0, 1):
+        srv = hc.HCServer(hc.ServerConfig(plain=plain), tuner)
+        tids = [srv.add_text(y, sigma=texts[i][1]) for i, y in enumerate(ydev)]
+        servers[plain] = (srv, tids)
+
+    def run_stream(plain, rq, arrivals, count):
+        srv, _ = servers[plain]
+        while srv.poll(65536, positions=False):
+            pass
+        l0 = hc.hc_kernel_launches()
+        ids = srv.replay(rq, arrivals)
+        srv.drain()
+        res = []
+        while len(res) < count:
+            res += srv.poll(65536, wait_us=100_000, positions=False)
+        launches = hc.hc_kernel_launches() - l0
+        pos = {rid: k for k, rid in enumerate(ids)}
+        span = (max(r["done_ns"] for r in res) - min(r["submit_ns"] for r in res)) / 1e9
+        return res, pos, span, launches
+
+    reps = max(1, args.served_reps)
     for rate in args.served_rates:
         count = max(200, int(rate * args.served_seconds))
         stream = hi.served_requests(texts, count, float(rate), seed=6 + rate)
-        reqs = [(0, yhost[ti][off:off + m]) for _, ti, m, off in stream]
         arrivals = [a for a, _, _, _ in stream]
-        entry = {"offered_req_per_s": rate, "requests": count}
-        counts = {}
+        entry = {"offered_req_per_s": rate, "requests": count, "repetitions": reps}
+        counts, acc = {}, {0: None, 1: None}
+        for plain in (0, 1):   # warm-up (untimed): the first 500 requests, back to back
+            tids = servers[plain][1]
+            rq = [(tids[ti], yhost[ti][off:off + m]) for _, ti, m, off in stream]
+            run_stream(plain, rq[:500], [0.0] * min(500, len(rq)), min(500, len(rq)))
+        for rep in range(reps):
+            for plain in ((0, 1) if rep % 2 == 0 else (1, 0)):
+                tids = servers[plain][1]
+                rq = [(tids[ti], yhost[ti][off:off + m]) for _, ti, m, off in stream]
+                res, pos, span, launches = run_stream(plain, rq, arrivals, count)
+                a = acc[plain] or {"lat": [], "span": 0.0, "bytes": 0, "batches": 0, "max_batch": 0,
+                                   "errors": 0, "launches": 0, "p99": []}
+                lat = [(r["done_ns"] - r["submit_ns"]) / 1e3 for r in res]
+                a["lat"] += lat
+                a["p99"].append(round(_pct(lat, 99), 1))
+                a["span"] += span
+                a["bytes"] += sum(texts[stream[pos[r["id"]]][1]][0] for r in res)
+                a["batches"] += len({r["batch"] for r in res})
+                a["max_batch"] = max(a["max_batch"], max(r["batch_size"] for r in res))
+                a["errors"] += sum(1 for r in res if r["status"] not in (hc.HC_OK, hc.HC_ERR_CAPACITY))
+                a["launches"] += launches
+                acc[plain] = a
+                cnt = {pos[r["id"]]: r["count"] for r in res}
+                if plain in counts and counts[plain] != cnt:
+                    counts[plain] = None          # a repetition disagreed with the first
+                else:
+                    counts.setdefault(plain, cnt)
         for plain in (0, 1):
-            srv = hc.HCServer(hc.ServerConfig(plain=plain), tuner)
-            tids = [srv.add_text(y, sigma=texts[i][1]) for i, y in enumerate(ydev)]
-            rq = [(tids[ti], x) for (_, ti, _, _), (_, x) in zip(stream, reqs)]
-            # warm-up (untimed): the first 500 requests of the stream, back to back
-            srv.replay(rq[:500], [0.0] * min(500, len(rq)))
-            srv.drain()
-            while srv.stats()["completed"] > 0 and srv.poll(65536, positions=False):
-                pass
-            l0 = hc.hc_kernel_launches()
-            ids = srv.replay(rq, arrivals)
-            srv.drain()
-            res = []
-            while len(res) < count:
-                res += srv.poll(65536, wait_us=100_000, positions=False)
-            st = srv.stats()
-            launches = hc.hc_kernel_launches() - l0
-            srv.destroy()
-            pos = {rid: k for k, rid in enumerate(ids)}
-            lat = [(r["done_ns"] - r["submit_ns"]) / 1e3 for r in res]
-            span = (max(r["done_ns"] for r in res) - min(r["submit_ns"] for r in res)) / 1e9
-            nbytes = sum(texts[stream[pos[r["id"]]][1]][0] for r in res)
-            bad = sum(1 for r in res if r["status"] not in (hc.HC_OK, hc.HC_ERR_CAPACITY))
-            counts[plain] = {pos[r["id"]]: r["count"] for r in res}
+            a = acc[plain]
+            st = servers[plain][0].stats()
             entry["plain" if plain else "batched"] = {
-                "p50_us": round(_pct(lat, 50), 1), "p99_us": round(_pct(lat, 99), 1),
-                "mean_us": round(float(np.mean(lat)), 1),
-                "achieved_req_per_s": round(count / span, 1),
-                "GBps": round(nbytes / span / GB, 3),
-                "batches": len({r["batch"] for r in res}),
-                "max_batch": max(r["batch_size"] for r in res),
-                "mean_batch": round(count / max(len({r["batch"] for r in res}), 1), 2),
+                "p50_us": round(_pct(a["lat"], 50), 1),
+                "p99_us": float(np.median(a["p99"])),
+                "p99_us_pooled": round(_pct(a["lat"], 99), 1),
+                "p99_us_per_rep": a["p99"], "mean_us": round(float(np.mean(a["lat"])), 1),
+                "achieved_req_per_s": round(count * reps / a["span"], 1),
+                "GBps": round(a["bytes"] / a["span"] / GB, 3),
+                "batches": a["batches"], "max_batch": a["max_batch"],
+                "mean_batch": round(count * reps / max(a["batches"], 1), 2),
                 "peak_admitted_MiB": round(st["peak_inflight_bytes"] / 2 ** 20, 2),
-                "errors": bad, "gpu_launches": launches,
+                "errors": a["errors"], "gpu_launches": a["launches"],
             }
-        entry["counts_equal"] = counts[0] == counts[1]
+        entry["counts_equal"] = counts.get(0) is not None and counts.get(0) == counts.get(1)
         entry["p99_ratio_plain_over_batched"] = round(
             entry["plain"]["p99_us"] / max(entry["batched"]["p99_us"], 1e-9), 3)
         loads.append(entry)
@@ -997,26 +1055,17 @@ def run_served(args, rank, world, local_rank):
     stream = hi.served_requests(texts, nsat, 1e9, seed=99)
     sat_counts = {}
     for plain in (0, 1):
-        srv = hc.HCServer(hc.ServerConfig(plain=plain), tuner)
-        tids = [srv.add_text(y, sigma=texts[i][1]) for i, y in enumerate(ydev)]
+        tids = servers[plain][1]
         rq = [(tids[ti], yhost[ti][off:off + m]) for _, ti, m, off in stream]
-        srv.replay(rq[:500], [0.0] * min(500, len(rq)))
-        srv.drain()
-        while srv.poll(65536, positions=False):
-            pass
-        ids = srv.replay(rq, [0.0] * len(rq))
-        srv.drain()
-        res = []
-        while len(res) < nsat:
-            res += srv.poll(65536, wait_us=100_000, positions=False)
-        srv.destroy()
-        pos = {rid: k for k, rid in enumerate(ids)}
-        span = (max(r["done_ns"] for r in res) - min(r["submit_ns"] for r in res)) / 1e9
+        run_stream(plain, rq[:500], [0.0] * min(500, len(rq)), min(500, len(rq)))
+        res, pos, span, _ = run_stream(plain, rq, [0.0] * len(rq), nsat)
         nbytes = sum(texts[stream[pos[r["id"]]][1]][0] for r in res)
         sat_counts[plain] = {pos[r["id"]]: r["count"] for r in res}
         sat["plain" if plain else "batched"] = {
             "req_per_s": round(nsat / span, 1), "GBps": round(nbytes / span / GB, 3),
             "mean_batch": round(nsat / max(len({r["batch"] for r in res}), 1), 2)}
+    for plain in (0, 1):
+        servers[plain][0].destroy()
     sat["requests"] = nsat
     sat["speedup_vs_plain"] = round(sat["batched"]["req_per_s"] / sat["plain"]["req_per_s"], 3)
     sat["counts_equal"] = sat_counts[0] == sat_counts[1]
@@ -1033,7 +1082,10 @@ def run_served(args, rank, world, local_rank):
                    "m": "log-uniform 2 .. 1024", "arrivals": "Poisson",
                    "offered_req_per_s": list(args.served_rates), "seconds_per_load": args.served_seconds,
                    "admission_GiB": 32, "q_alpha": "autotuned (sigma in {4, 20, 95}, m 2 .. 1024)",
-                   "latency": "scheduled arrival -> result copied on the host"},
+                   "latency": "scheduled arrival -> result copied on the host",
+                   "p99": "median over the repetitions of each repetition's p99 (a host stall of tens of "
+                          "ms in one repetition moves a pooled p99 by orders of magnitude; the pooled "
+                          "figure is p99_us_pooled)"},
         "p50_us": top["batched"]["p50_us"], "p99_us": top["batched"]["p99_us"],
         "loads": loads, "saturation": sat, "tune_s": round(tune_s, 2),
         "gpu_launches": int(sum(ld["batched"]["gpu_launches"] for ld in loads)),
@@ -1161,7 +1213,7 @@ def other_workloads(args, local_rank):
         "cells": {k: {"GBps": v["GBps"], "kernel": v["kernel"], "hbm_frac": v["hbm_frac"]}
                   for k, v in sk["cells"].items()}}
     a = copy.copy(args)
-    a.workload, a.steps, a.warmup = "batched", 3, 3
+    a.workload, a.steps, a.warmup, a.tuner_table = "batched", 3, 3, ""
     bt = run_batched(a, 0, 1, local_rank)
     out["batched"] = {k: bt[k] for k in (
         "metric", "value", "unit", "ms_per_step", "steps", "queries_per_s", "paper_params_GBps",
@@ -1175,10 +1227,12 @@ def other_workloads(args, local_rank):
         "metric": sv["metric"], "value": sv["value"], "unit": sv["unit"],
         "p50_us": sv["p50_us"], "p99_us": sv["p99_us"], "config": sv["config"],
         "loads": [{"offered_req_per_s": ld["offered_req_per_s"], "requests": ld["requests"],
-                   "counts_equal": ld["counts_equal"],
-                   "batched": {k: ld["batched"][k] for k in ("p50_us", "p99_us", "achieved_req_per_s", "GBps",
+                   "repetitions": ld["repetitions"], "counts_equal": ld["counts_equal"],
+                   "batched": {k: ld["batched"][k] for k in ("p50_us", "p99_us", "p99_us_per_rep",
+                                                             "p99_us_pooled", "achieved_req_per_s", "GBps",
                                                              "mean_batch", "gpu_launches")},
-                   "plain": {k: ld["plain"][k] for k in ("p50_us", "p99_us", "achieved_req_per_s", "GBps")}}
+                   "plain": {k: ld["plain"][k] for k in ("p50_us", "p99_us", "p99_us_per_rep",
+                                                         "p99_us_pooled", "achieved_req_per_s", "GBps")}}
                   for ld in sv["loads"]],
         "saturation": sv["saturation"], "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"]}
     out["other_workloads_wall_s"] = round(time.perf_counter() - t0, 1)

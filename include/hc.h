@@ -108,8 +108,10 @@ int hc_filter_to_device(hc_filter *f);
  * with a filter copies it to the device (see hc_filter_to_device).  Each call
  * takes a stream-ordered workspace from the library's memory pool and gives
  * it back after its kernels: 16 bytes per warp plus 4 bytes per spilled
- * position (by default min(n-m+1, max(cap, 2^20)) of them), or for the
- * single-pass dense form (m = q) 8 bytes per tile of 8192 window starts;
+ * position (by default min(n-m+1, max(cap, 2^20)) of them), for the
+ * dense form's bitmap (m = q, hc_search_opts.bitmap) 16 bytes per warp plus
+ * one bit per window start, or for the single-pass dense form 8 bytes per
+ * tile of 8192 window starts;
  * the pool keeps freed memory for reuse.  n < m is not an error: the count is 0.  Errors:
  * HC_ERR_ARG, HC_ERR_CUDA, HC_ERR_NOMEM; a device wait that gave up is
  * reported by the next hc_search/hc_check_status.
@@ -177,6 +179,14 @@ typedef struct hc_search_opts {
                                once per test that passes, instead of for
                                every window; 0 -- HC's position test per
                                window */
+    int bitmap;             /* dense mode: 1 -- the scan writes one bit per
+                               window start (n / 8 bytes of workspace) and
+                               each warp's count, and the emit kernel turns
+                               the bits into positions: no work per
+                               occurrence in the scan and no spill round
+                               trip, for patterns with many occurrences;
+                               0 -- spill regions (the automatic choice).
+                               Excludes single_pass = 1. */
 } hc_search_opts;
 
 /* hc_search_ex: hc_search_async with explicit launch options (opts may be
@@ -245,6 +255,8 @@ typedef struct hc_tune_entry {
     int q, alpha, lane_bytes, mode;
     int sentinel;           /* 1: the staged mode's sentinel form
                                (hc_search_opts.sentinel) */
+    int bitmap;             /* 1: the dense mode's bitmap form
+                               (hc_search_opts.bitmap) */
     uint64_t m;
     double gbps;
 } hc_tune_entry;
@@ -312,7 +324,8 @@ void hc_batch_destroy(hc_batch *b);
  * hc_tuner_lookup: the cell nearest to (sigma, m) on log scales, q clamped
  *   to m (the paper's choice when the table is empty).
  * hc_tuner_save / hc_tuner_load: the table as text, one cell per line
- *   ("sigma m q alpha lane_bytes mode gbps"); load adds to the table.
+ *   ("sigma m q alpha lane_bytes mode gbps sentinel bitmap"; the last two
+ *   columns are optional, 0 when absent); load adds to the table.
  * Errors: HC_ERR_ARG, HC_ERR_NOMEM, HC_ERR_CUDA; HC_ERR_STATE for an
  * unreadable or malformed file. */
 enum { HC_TUNE_BATCHED = 0, HC_TUNE_SINGLE = 1 };
@@ -389,11 +402,14 @@ typedef struct hc_server_config {
     int batch_only;         /* 1: every request runs the batched kernels (0:
                                a lone request, and m = q requests in batches
                                of <= 16, run the single-search kernels) */
-    uint64_t max_batch_bytes; /* text bytes per batch (a single larger request
-                               still runs, alone); a backlog is cut into
-                               batches of at most this much text that run on
-                               several streams and complete one by one;
-                               0 = 64 MiB */
+    uint64_t max_batch_bytes; /* text bytes per batch while the queue is
+                               short (a single larger request still runs,
+                               alone), so that a request arriving behind a
+                               batch waits for little text; when more than
+                               max_inflight times this much text is queued,
+                               a batch may take queued text / max_inflight
+                               instead, so that a backlog drains in few
+                               large batches; 0 = 64 MiB */
 } hc_server_config;
 
 typedef struct hc_server_request {

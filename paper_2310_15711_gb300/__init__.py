@@ -271,13 +271,14 @@ class SearchOpts(ctypes.Structure):
                 ("stages", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("mode", ctypes.c_int), ("spill_entries", ctypes.c_uint64),
                 ("speculate", ctypes.c_int), ("pos32", ctypes.c_int),
-                ("single_pass", ctypes.c_int), ("tile_steps", ctypes.c_int), ("sentinel", ctypes.c_int)]
+                ("single_pass", ctypes.c_int), ("tile_steps", ctypes.c_int), ("sentinel", ctypes.c_int),
+                ("bitmap", ctypes.c_int)]
 
     def __init__(self, lane_bytes=0, stages=0, ctas_per_sm=0, spill_entries=0, mode=0,
-                 speculate=0, pos32=0, single_pass=0, tile_steps=0, sentinel=0):
+                 speculate=0, pos32=0, single_pass=0, tile_steps=0, sentinel=0, bitmap=0):
         super().__init__(ctypes.sizeof(SearchOpts), int(lane_bytes), int(stages),
                          int(ctas_per_sm), int(mode), int(spill_entries), int(speculate), int(pos32),
-                         int(single_pass), int(tile_steps), int(sentinel))
+                         int(single_pass), int(tile_steps), int(sentinel), int(bitmap))
 
 
 class HCFilter:
@@ -419,11 +420,11 @@ class TuneEntry(ctypes.Structure):
     """hc_tune_entry."""
     _fields_ = [("sigma", ctypes.c_int), ("q", ctypes.c_int), ("alpha", ctypes.c_int),
                 ("lane_bytes", ctypes.c_int), ("mode", ctypes.c_int), ("sentinel", ctypes.c_int),
-                ("m", ctypes.c_uint64), ("gbps", ctypes.c_double)]
+                ("bitmap", ctypes.c_int), ("m", ctypes.c_uint64), ("gbps", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k in ("sigma", "m", "q", "alpha", "lane_bytes", "mode", "gbps",
-                                              "sentinel")}
+                                              "sentinel", "bitmap")}
 
 
 class HCTuner:

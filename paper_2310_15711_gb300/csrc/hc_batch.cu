@@ -125,25 +125,30 @@ __global__ void __launch_bounds__(kThreads)
   uint32_t* slots = reinterpret_cast<uint32_t*>(xs + lay.x_bytes);
   uint8_t* ring = reinterpret_cast<uint8_t*>(slots + kSlots * kThreads) +
                   static_cast<size_t>(warp) * lay.ring_bytes;
+  uint32_t staged_query = ~0u;  // query whose arguments, F and x are in shared memory
   while (true) {
     if (tid == 0) s_tile = atomicAdd(counter, 1ull);
     __syncthreads();
     const unsigned long long t = s_tile;
     if (t >= ntiles) break;
     const BatchTile bt = tiles[t];
-    load_args(&sa, args + bt.query);
-    __syncthreads();
-    for (uint32_t i = tid; i < sa.fwords; i += kThreads) Fs[i] = sa.F[i];
-    for (uint32_t i = tid; i < sa.x_smem && i < static_cast<uint32_t>(sa.m); i += kThreads)
-      xs[i] = sa.x[i];
-    __syncthreads();
+    if (bt.query != staged_query) {
+      // a new query: its arguments, filter and pattern (tiles of one query
+      // are claimed one after another, so this is rare)
+      load_args(&sa, args + bt.query);
+      __syncthreads();
+      stage_words(Fs, sa.F, sa.fwords);
+      stage_bytes(xs, sa.x, min(sa.x_smem, static_cast<uint32_t>(sa.m)));
+      __syncthreads();
+      staged_query = bt.query;
+    }
     const uint8_t* xv = sa.x_smem ? xs : sa.x;
     const unsigned long long r = static_cast<unsigned long long>(bt.first_record) + warp;
     if (r < sa.records) {
       if (sa.stages > 0) stream_q<true>(sa, r, Fs, xv, slots, ring, bars[warp]);
       else stream_q<false>(sa, r, Fs, xv, slots, ring, bars[warp]);
     }
-    __syncthreads();  // F, x and the arguments are replaced by the next tile
+    __syncthreads();  // s_tile (and F, x and the arguments) may be replaced by the next tile
   }
 }
 

@@ -40,6 +40,7 @@ struct BatchLayout {
 struct QueryParams {
   int q = 0, alpha = 0, lane_bytes = 0, mode = 0;
   int sentinel = 0;  // single searches in the staged mode: the sentinel form
+  int bitmap = 0;    // single searches in the dense mode: the bitmap form
 };
 
 // Queries are grouped by the number of CTAs per SM their own shared-memory

@@ -456,4 +456,112 @@ KernelFn dense_single_pass_kernel_for_q(int q) {
 
 KernelFn single_pass_init_kernel() { return hc_single_pass_init_kernel; }
 
+// ---------------------------------------------------------------------------
+// Emit of the dense scan's bitmap form: the scan's warp r (record r) has set
+// bit j of group g for each occurrence at window 16g + j of its chunks and
+// written its total; warp r of this grid writes record r's positions.  Its
+// output offset is the sum of the totals before it: one total per earlier
+// CTA of the scan (blk_total) plus the earlier warps of its own CTA.  It then
+// walks the record's bits in text order, 1024 windows per round (one 32-bit
+// word per lane; the words of kBitmapWords rounds are loaded at once, and a
+// round without a set bit costs one vote): a warp scan of the words'
+// popcounts gives each lane its first slot, the lane writes its window
+// starts into the warp's shared-memory buffer in order, and the warp copies
+// the buffer to the output with consecutive stores.  (Splitting a record's
+// chunks over the 8 warps of a CTA, with per-chunk counts from the scan,
+// measured slower on GB300 for the patterns this form serves: those with
+// many occurrences, where every round has bits.)
+namespace {
+constexpr int kBitmapWords = 8;
+constexpr int kBitmapRound = 1024;  // windows per round (32 lanes x 32 bits)
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads, 4) hc_emit_bitmap_kernel(const SearchArgs a) {
+  __shared__ uint32_t s_buf[kWarps][kBitmapRound];
+  __shared__ unsigned long long s_red[kWarps];
+  pdl_launch_dependents();  // the next search's scan may be scheduled; it waits for this grid
+  pdl_wait();               // the scan grid has completed: its bits and totals are visible
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long p = 0;
+  for (unsigned long long k = tid; k < blockIdx.x; k += kThreads) p += a.blk_total[k];
+  p = warp_sum_u64(p);
+  if (lane == 0) s_red[warp] = p;
+  __syncthreads();
+  const unsigned long long rb = static_cast<unsigned long long>(blockIdx.x) * kWarps;
+  unsigned long long P = 0;
+  for (int w = 0; w < kWarps; ++w) P += s_red[w];
+  for (int w = 0; w < warp; ++w) P += a.cta_total[rb + w];
+  const unsigned long long r = rb + warp;
+  const unsigned long long T = a.cta_total[r];
+  if (r + 1 == a.records && lane == 0) *a.count_out = P + T;
+  const unsigned long long c0 = r * a.chunks_per_cta;
+  const unsigned long long c1 = min(c0 + a.chunks_per_cta, a.num_chunks);
+  if (T == 0 || c0 >= c1 || P >= a.cap) return;
+  const unsigned long long W0 = c0 * a.C;              // a multiple of 256
+  const unsigned long long W1 = min(c1 * a.C, a.nwin);
+  const unsigned long long end = min(P + T, a.cap);    // output slots of this record
+  const uint32_t* bits = reinterpret_cast<const uint32_t*>(a.bitmap);
+  uint32_t* buf = s_buf[warp];
+  for (unsigned long long w = W0; w < W1 && P < end; w += static_cast<unsigned long long>(kBitmapRound) * kBitmapWords) {
+    uint32_t v[kBitmapWords];
+#pragma unroll
+    for (int u = 0; u < kBitmapWords; ++u) {
+      // bits of windows at or past W1 are cleared: the scan leaves the groups
+      // past the last window of the text unwritten
+      const unsigned long long wl = w + static_cast<unsigned long long>(u * 32 + lane) * 32;
+      v[u] = 0u;
+      if (wl < W1) {
+        if (HC_IN_BOUNDS(wl / 32 < a.num_chunks * (a.C / 32))) v[u] = __ldcs(bits + wl / 32);
+        if (W1 - wl < 32) v[u] &= (1u << (W1 - wl)) - 1u;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBitmapWords; ++u) {
+      if (!__any_sync(0xffffffffu, v[u] != 0u)) continue;
+      const uint32_t cnt = static_cast<uint32_t>(__popc(v[u]));
+      const uint32_t incl = warp_incl_scan_u32(cnt);
+      const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      // window of this lane's bit 0, counted from W0 (< 2^32: a record's
+      // windows are fewer than 2^32)
+      const uint32_t rel = static_cast<uint32_t>(w - W0) + static_cast<uint32_t>(u * 32 + lane) * 32u;
+      uint32_t o = incl - cnt, b = v[u];
+      while (b) {
+        if (HC_IN_BOUNDS(o < static_cast<uint32_t>(kBitmapRound))) buf[o] = rel + static_cast<uint32_t>(__ffs(b) - 1);
+        ++o;
+        b &= b - 1u;
+      }
+      __syncwarp();
+      const uint32_t lim = static_cast<uint32_t>(min(static_cast<unsigned long long>(tot), end - P));
+      if (a.pos32) {
+        uint32_t* out = reinterpret_cast<uint32_t*>(a.pos) + P;
+        const uint32_t b32 = static_cast<uint32_t>(W0);
+        for (uint32_t i = lane; i < lim; i += 32) out[i] = b32 + buf[i];
+      } else {
+        unsigned long long* out = a.pos + P;
+        for (uint32_t i = lane; i < lim; i += 32) out[i] = W0 + buf[i];
+      }
+      __syncwarp();  // the buffer is free again
+      P += tot;
+      if (P >= end) break;
+    }
+  }
+}
+
+KernelFn emit_bitmap_kernel() { return hc_emit_bitmap_kernel; }
+
+// This translation unit's bound-violation counter (checked build).
+int take_bound_violations_dense(uint64_t* count) {
+  *count = 0;
+#ifdef HC_CHECKED
+  unsigned long long v = 0, zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_bound_violations, sizeof v);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bound_violations, &zero, sizeof zero);
+  if (e != cudaSuccess) return cuda_error(e, "bound violation counter");
+  *count = v;
+  return HC_OK;
+#else
+  return HC_ERR_STATE;
+#endif
+}
+
 }  // namespace hc

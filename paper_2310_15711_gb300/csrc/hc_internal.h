@@ -101,6 +101,7 @@ void timing_end(const TimingToken& t, cudaStream_t stream);
 // hc_search.cu and hc_batch.cu since the last call (then reset).
 int take_bound_violations_search(uint64_t* count);
 int take_bound_violations_batch(uint64_t* count);
+int take_bound_violations_dense(uint64_t* count);
 
 // Copies the filter to the current device (once).  Returns an HC_* code.
 int filter_to_device(Filter* f);
@@ -141,6 +142,10 @@ struct SearchPlan {
   KernelFn init = nullptr;
   int tile_chunks = 0, flag_steps = 0;
   unsigned long long max_tiles = 0;  // descriptors in the workspace
+  // bitmap form of the dense scan: one bit per window start in the
+  // workspace instead of spill regions; the emit kernel expands the bits
+  bool bitmap = false;
+  unsigned long long bitmap_bytes = 0;
 };
 
 int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, int dev,
@@ -148,6 +153,8 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
 // The single-pass dense scan for a given q and its init kernel (hc_dense.cu).
 KernelFn dense_single_pass_kernel_for_q(int q);
 KernelFn single_pass_init_kernel();
+// The emit kernel of the dense scan's bitmap form (hc_dense.cu).
+KernelFn emit_bitmap_kernel();
 // Device address of the library's status word on the current device.
 unsigned int* status_word();
 int launch_planned(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,

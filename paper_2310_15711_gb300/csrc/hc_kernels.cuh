@@ -26,6 +26,9 @@ constexpr int kEmitUnits = 8;               // 8-byte region loads in flight per
 constexpr int kSinglePassMaxSteps = 64;     // 512-window steps per single-pass tile (a u64 of flags)
 constexpr int kSinglePassTileSteps = 16;    // default steps per single-pass tile
 constexpr unsigned long long kSinglePassGroup = 64;  // tiles per group of the single-pass counts
+constexpr int kQueueCap = 256;              // dense scan: candidate lanes queued per warp (u16 each)
+constexpr int kDirectLanes = 16;            // dense scan: candidate lanes from which a step is finished at once
+constexpr int kTwoStageLanes = 6;           // dense scan, q >= 5: mean candidate lanes per step above which one stage
 
 
 // Bytes of one staging buffer: head (< 16) + C + m - 1 bytes of text rounded
@@ -85,6 +88,10 @@ struct SearchArgs {
   unsigned long long num_tiles, num_groups;
   int tile_chunks;
   int flag_steps;
+  // bitmap form of the dense scan (m = q): bit j of bitmap[g] is set iff
+  // window 16g + j is an occurrence (chunk c's groups start at c * C / 16);
+  // the emit kernel turns the bits into positions.  NULL: spill regions.
+  uint16_t* bitmap;
 };
 
 // ---------------------------------------------------------------------------
@@ -529,6 +536,56 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
   return cnt;
 }
 
+// Copies `words` 32-bit words (F) from global to shared memory, each thread
+// issuing up to eight loads before its stores (one round of memory latency
+// per 32 KB instead of one per 1 KB): 16-byte loads when both pointers are
+// 16-byte aligned and `words` is a multiple of 4, else 4-byte loads.  Every
+// thread of the CTA calls it; the caller synchronises before reading dst.
+__device__ __forceinline__ void stage_words(uint32_t* dst, const uint32_t* src, uint32_t words) {
+  const uint32_t tid = threadIdx.x;
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 && (words & 3u) == 0) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    const uint32_t n4 = words >> 2;
+    for (uint32_t i0 = tid; i0 < n4; i0 += 8u * kThreads) {
+      uint4 v[8];
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u)
+        if (i0 + u * kThreads < n4) v[u] = __ldg(s4 + i0 + u * kThreads);
+#pragma unroll
+      for (uint32_t u = 0; u < 8; ++u)
+        if (i0 + u * kThreads < n4) d4[i0 + u * kThreads] = v[u];
+    }
+    return;
+  }
+  for (uint32_t i0 = tid; i0 < words; i0 += 8u * kThreads) {
+    uint32_t v[8];
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u)
+      if (i0 + u * kThreads < words) v[u] = __ldg(src + i0 + u * kThreads);
+#pragma unroll
+    for (uint32_t u = 0; u < 8; ++u)
+      if (i0 + u * kThreads < words) dst[i0 + u * kThreads] = v[u];
+  }
+}
+
+// Copies n bytes (the pattern x) from global to shared memory: 16-byte loads
+// for the whole 16-byte blocks when both pointers are 16-byte aligned, bytes
+// for the rest; nothing past src[n - 1] is read.  Called by every thread of
+// the CTA; the caller synchronises.
+__device__ __forceinline__ void stage_bytes(uint8_t* dst, const uint8_t* src, uint32_t n) {
+  const uint32_t tid = threadIdx.x;
+  uint32_t done = 0;
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+    const uint32_t n16 = n >> 4;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (uint32_t i = tid; i < n16; i += kThreads) d4[i] = __ldg(s4 + i);
+    done = n16 << 4;
+  }
+  for (uint32_t i = done + tid; i < n; i += kThreads) dst[i] = src[i];
+}
+
 // End of a single-search scan CTA: the sum of its kWarps records' totals
 // (each written by lane 0 of its warp) into blk_total[blockIdx.x], so that
 // the emit kernel sums one total per CTA instead of one per warp.  Every
@@ -851,7 +908,7 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
         uint32_t* Fs = reinterpret_cast<uint32_t*>(smem);
         uint32_t* slots = Fs + ((a.fwords + 3u) & ~3u);
         if (!f_loaded) {
-          for (uint32_t k = tid; k < a.fwords; k += kThreads) Fs[k] = a.F[k];
+          stage_words(Fs, a.F, a.fwords);
           __syncthreads();
           f_loaded = true;
         }

@@ -66,9 +66,8 @@ __global__ void __launch_bounds__(kThreads, 4) hc_scan_kernel(const SearchArgs a
   const uint32_t f_bytes = (a.fwords * 4u + 15u) & ~15u;
   uint8_t* xs = smem + f_bytes;
   uint32_t* slots = reinterpret_cast<uint32_t*>(xs + a.x_smem);
-  for (uint32_t i = tid; i < a.fwords; i += kThreads) Fs[i] = a.F[i];
-  for (uint32_t i = tid; i < a.x_smem && i < static_cast<uint32_t>(a.m); i += kThreads)
-    xs[i] = a.x[i];
+  stage_words(Fs, a.F, a.fwords);
+  stage_bytes(xs, a.x, min(a.x_smem, static_cast<uint32_t>(a.m)));
   const uint8_t* xv = a.x_smem ? xs : a.x;
   __syncthreads();
   // launched as a programmatic dependent of the previous search's emit
@@ -95,10 +94,21 @@ __global__ void __launch_bounds__(kThreads, 4) hc_scan_kernel(const SearchArgs a
 //
 // Every warp is an independent stream: it owns a contiguous range of chunks
 // (record w = blockIdx.x * 8 + warp), stages them through its own ring of
-// shared-memory buffers with bulk copies on its own mbarriers, and appends
-// its matches -- compacted in order with ballots -- straight to its own
-// spill region.  There is no CTA-wide barrier in the loop.
-template <int Q>
+// shared-memory buffers with bulk copies on its own mbarriers, queues the
+// lanes that hold a candidate in a step, finishes them 32 at a time and
+// appends the matches, in order, straight to its own spill region.  There is
+// no CTA-wide barrier in the loop.
+//
+// Bitmap form (BM): instead, every lane turns its 16 windows of a step into
+// a 16-bit mask, and the warp writes the masks as the text's window bitmap
+// (bit j of group g: window 16g + j of the chunk; a lane's windows start
+// `head` windows before a group boundary, so group g joins the upper bits of
+// one lane's mask with the lower bits of the next lane's, the last lane's
+// carried over to the next step).  The warp's total goes to its record; the
+// emit kernel expands the bits.  No work per occurrence in the scan, and
+// n / 8 bytes written and read back instead of 4 bytes per occurrence each
+// way: the form for patterns with many occurrences.
+template <int Q, bool BM>
 __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem, uint64_t* wb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned long long w_id = static_cast<unsigned long long>(blockIdx.x) * kWarps + warp;
@@ -114,6 +124,9 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
   }
   const int nst = a.stages;
   uint8_t* stages = smem + static_cast<size_t>(warp) * nst * a.stage_bytes;
+  // spill form: the warp's queue of candidate lanes, after all warps' rings
+  uint16_t* queue = reinterpret_cast<uint16_t*>(smem + static_cast<size_t>(kWarps) * nst * a.stage_bytes) +
+                    static_cast<size_t>(warp) * kQueueCap;
   const int nchunks = static_cast<int>(c1 - c0);
 
   // the chunk's bytes go to stage (i % nst); the warp's lane 0 drives the copies
@@ -148,7 +161,9 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
   int single_left = 0;  // chunks left in the one-stage byte test (q >= 5)
 
   const unsigned long long S = a.region_entries;
-  uint32_t* region = a.region + w_id * S;
+  uint32_t* region = BM ? nullptr : a.region + w_id * S;
+  const int hd = a.head;
+  const int gchunk = static_cast<int>(a.C / 16u);  // bitmap groups per chunk
   unsigned long long T = 0;                 // matches so far in this warp's range
   unsigned long long overflow = kNoOverflow;
   bool ok = true;
@@ -176,8 +191,10 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
     // 16-byte aligned shared-memory offset; windows outside [0, wins) are
     // masked
     // q >= 5: a two-stage byte test (columns 0, 1, 4, 5 first; the others
-    // only in steps where some lane has a candidate) while the first stage
-    // rejects most steps, else the one-stage test for the next 16 chunks
+    // only for the lanes with a candidate) while the first stage leaves few
+    // candidates (the spill form: at most kTwoStageLanes lanes per step on
+    // average; the bitmap form: candidates in at most half the steps), else
+    // the one-stage test for the next 16 chunks
     const bool two = Q >= 5 && single_left == 0;
     int second = 0, steps = 0;
     // The first (or only) stage of the byte test for the step at `base`
@@ -202,65 +219,76 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
       // positions above a zero byte may be wrong, so they are not used)
       return (live && filter_passes) ? any_zero_byte4(dg) : 0u;
     };
-    // The rest of a step in which some lane has a candidate: the second
-    // stage, the exact per-window flags and the ordered writes.
-    auto finish_step = [&](int base, const uint32_t (&Tw)[6], uint32_t (&dg)[4], uint32_t cand) {
-      const int w0 = base + 16 * lane;      // first window of this lane
-      uint32_t cand_lanes;
-      if (two) {
-        ++second;
-        if (cand != 0u) {
-          or_columns<Q, 2, 0, 0>(Tw, xrep, dg);
-          cand = any_zero_byte4(dg);
-        }
-        cand_lanes = __ballot_sync(0xffffffffu, cand != 0u);
-        if (cand_lanes == 0u) return;
-      } else {
-        cand_lanes = __ballot_sync(0xffffffffu, cand != 0u);
-      }
-      // exact zero-byte test: bit 8k+7 of zg[g] is set iff window w0+4g+k
-      // equals x (bit 7 of a byte set iff the byte is 0)
-      uint32_t zg[4] = {0u, 0u, 0u, 0u};
-      if (cand != 0u) {
+    // The steps' candidate lanes wait in the warp's queue (entry: step
+    // index << 5 | lane, in step order, lanes in order within a step) and
+    // are finished 32 at a time, one per lane: the lane tests its 16 windows
+    // again with every column, takes the exact per-window flags, and the
+    // warp writes the matches in window order to the spill region.  A step
+    // with one or two candidates then costs a vote and a queue store
+    // instead of a warp-wide finish.
+    int qn = 0;   // entries in the queue
+    auto flush = [&]() {
+      for (int e0 = 0; e0 < qn; e0 += 32) {
+        const int e = e0 + lane;
+        uint32_t mbits = 0;
+        int w0 = 0;
+        if (e < qn) {
+          const uint32_t ent = queue[e];
+          w0 = -a.head + 512 * static_cast<int>(ent >> 5) + 16 * static_cast<int>(ent & 31u);
+          const uint32_t o = static_cast<uint32_t>(a.head + w0);  // >= 0, 16-byte aligned: a live lane's
+          HC_IN_BOUNDS(o + 24u <= a.stage_bytes);
+          const uint4 A = *reinterpret_cast<const uint4*>(sb + o);
+          const uint2 B = *reinterpret_cast<const uint2*>(sb + o + 16);
+          const uint32_t Tw[6] = {A.x, A.y, A.z, A.w, B.x, B.y};
+          uint32_t dg[4] = {0u, 0u, 0u, 0u};
+          or_columns<Q, 0, 0, 0>(Tw, xrep, dg);
+          // exact zero-byte test: bit 8k+7 of zg is set iff window w0+4g+k
+          // equals x; packed to bit 4g+k of mbits
 #pragma unroll
-        for (int g = 0; g < 4; ++g) zg[g] = ~(((dg[g] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | dg[g] | 0x7f7f7f7fu);
-        if (w0 < 0 || w0 + 16 > wins) {
-          // windows outside [0, wins): vm holds the valid ones in window
-          // order; nibble g of vm spread to bits 7, 15, 23, 31 masks zg[g]
-          uint32_t vm = 0xffffu;
-          if (w0 < 0) vm &= 0xffffu << min(-w0, 16);
-          if (w0 + 16 > wins) vm &= 0xffffu >> (16 - (wins - w0));
-#pragma unroll
-          for (int g = 0; g < 4; ++g)
-            zg[g] &= ((((vm >> (4 * g)) & 0xfu) * 0x00204081u) & 0x01010101u) << 7;
-        }
-      }
-      if (__popc(cand_lanes) <= 8) {
-        // few lanes with a candidate (occurrences are sparse): when no lane
-        // holds two, each lane's output offset is the number of lanes below
-        // it that hold one -- a single ballot, no scan.  pk has bit 8k+g set
-        // for window w0+4g+k.
-        uint32_t pk = 0;
-#pragma unroll
-        for (int g = 0; g < 4; ++g) pk |= zg[g] >> (7 - g);
-        const uint32_t one = static_cast<uint32_t>(__popc(pk));
-        if (!__any_sync(0xffffffffu, one > 1u)) {
-          const uint32_t holders = __ballot_sync(0xffffffffu, one != 0u);
-          if (store && one != 0u) {
-            const int p = __ffs(pk) - 1;
-            const unsigned long long out = t + static_cast<unsigned long long>(__popc(holders & ((1u << lane) - 1u)));
-            if (out < S) region[out] = rel + static_cast<uint32_t>(w0 + 4 * (p & 7) + (p >> 3));
+          for (int g = 0; g < 4; ++g) {
+            const uint32_t zg = ~(((dg[g] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | dg[g] | 0x7f7f7f7fu);
+            mbits |= ((zg >> 7) * 0x01020408u >> 24) << (4 * g);
           }
-          t += static_cast<unsigned long long>(__popc(holders));
-          return;
+          if (w0 < 0) mbits &= 0xffffu << min(-w0, 16);
+          if (w0 + 16 > wins) mbits &= 0xffffu >> (16 - max(wins - w0, 0));
         }
+        const uint32_t mine = static_cast<uint32_t>(__popc(mbits));
+        const uint32_t incl = warp_incl_scan_u32(mine);
+        if (store) {
+          unsigned long long out = t + (incl - mine);
+          while (mbits) {
+            const int k = __ffs(mbits) - 1;
+            if (out < S) region[out] = rel + static_cast<uint32_t>(w0 + k);
+            ++out;
+            mbits &= mbits - 1u;
+          }
+        }
+        t += __shfl_sync(0xffffffffu, incl, 31);
       }
-      // general case: the lane's flags in window order (bit i: window w0+i)
+      qn = 0;
+    };
+    // appends the candidate lanes `cl` of step sidx
+    auto enqueue = [&](int sidx, uint32_t cl) {
+      if ((cl >> lane) & 1u) queue[qn + __popc(cl & ((1u << lane) - 1u))] = static_cast<uint16_t>((sidx << 5) | lane);
+      qn += __popc(cl);
+    };
+    // a step in which most lanes hold a candidate is finished at once, from
+    // the column differences at hand (the queue, in window order before it,
+    // is flushed first)
+    auto finish_now = [&](int base, const uint32_t (&Tw)[6], uint32_t (&dg)[4], uint32_t cand) {
+      if (qn != 0) flush();
+      const int w0 = base + 16 * lane;
       uint32_t mbits = 0;
+      if (cand != 0u) {
+        if (two) or_columns<Q, 2, 0, 0>(Tw, xrep, dg);
 #pragma unroll
-      for (int g = 0; g < 4; ++g) mbits |= ((zg[g] >> 7) * 0x01020408u >> 24) << (4 * g);
-      // in-order compaction (lanes in order, a lane's windows in order),
-      // written straight to the spill region
+        for (int g = 0; g < 4; ++g) {
+          const uint32_t zg = ~(((dg[g] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | dg[g] | 0x7f7f7f7fu);
+          mbits |= ((zg >> 7) * 0x01020408u >> 24) << (4 * g);
+        }
+        if (w0 < 0) mbits &= 0xffffu << min(-w0, 16);
+        if (w0 + 16 > wins) mbits &= 0xffffu >> (16 - max(wins - w0, 0));
+      }
       const uint32_t mine = static_cast<uint32_t>(__popc(mbits));
       const uint32_t incl = warp_incl_scan_u32(mine);
       if (store) {
@@ -273,23 +301,108 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
         }
       }
       t += __shfl_sync(0xffffffffu, incl, 31);
-        };
+    };
+    if constexpr (BM) {
+      // this lane's exact 16-bit mask (bit i: window w0 + i) from complete
+      // column differences; windows outside [0, wins) cleared
+      auto exact = [&](int base, const uint32_t (&dg)[4]) -> uint32_t {
+        const int w0 = base + 16 * lane;
+        uint32_t mb = 0;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const uint32_t zg = ~(((dg[g] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | dg[g] | 0x7f7f7f7fu);
+          mb |= ((zg >> 7) * 0x01020408u >> 24) << (4 * g);
+        }
+        if (w0 < 0) mb &= 0xffffu << min(-w0, 16);
+        if (w0 + 16 > wins) mb &= 0xffffu >> (16 - max(wins - w0, 0));
+        return mb;
+      };
+      uint16_t* bm = a.bitmap + c * static_cast<unsigned long long>(gchunk);
+      uint32_t carry = 0;      // the last lane's mask of the previous step
+      uint32_t chunk_cnt = 0;  // this lane's matches in the chunk
+      int sidx = 0;            // step index in the chunk
+      // group 32 * sidx + lane - 1 from the previous lane's mask (upper
+      // 16 - hd bits) and this lane's (lower hd bits)
+      auto put = [&](uint32_t mb) {
+        const uint32_t up = __shfl_up_sync(0xffffffffu, mb, 1);
+        const uint32_t prev = lane == 0 ? carry : up;
+        carry = __shfl_sync(0xffffffffu, mb, 31);
+        const int G = 32 * sidx + lane - 1;
+        if (G >= 0 && G < gchunk) bm[G] = static_cast<uint16_t>(((prev >> hd) | (mb << (16 - hd))) & 0xffffu);
+        chunk_cnt += static_cast<uint32_t>(__popc(mb));
+        ++sidx;
+      };
+      for (int base = -a.head; base < wins; base += 1024) {
+        uint32_t Tw0[6], dg0[4], Tw1[6], dg1[4];
+        const uint32_t k0 = test(base, Tw0, dg0);
+        const uint32_t k1 = test(base + 512, Tw1, dg1);
+        steps += 2;
+        uint32_t m0 = 0u, m1 = 0u;
+        if (two) {
+          // the other columns only where the first stage left a candidate
+          if (__any_sync(0xffffffffu, (k0 | k1) != 0u)) {
+            second += (__any_sync(0xffffffffu, k0 != 0u) ? 1 : 0) + (__any_sync(0xffffffffu, k1 != 0u) ? 1 : 0);
+            if (k0 != 0u) {
+              or_columns<Q, 2, 0, 0>(Tw0, xrep, dg0);
+              m0 = exact(base, dg0);
+            }
+            if (k1 != 0u) {
+              or_columns<Q, 2, 0, 0>(Tw1, xrep, dg1);
+              m1 = exact(base + 512, dg1);
+            }
+          }
+        } else if (__any_sync(0xffffffffu, (k0 | k1) != 0u)) {
+          // one stage: dg is complete; a lane without a candidate (or past
+          // the end, or with F[h(x)] = 0) has no match
+          if (k0 != 0u) m0 = exact(base, dg0);
+          if (k1 != 0u) m1 = exact(base + 512, dg1);
+        }
+        put(m0);
+        put(m1);
+      }
+      // the last group, whose upper bits lie past the last step
+      const int G = 32 * sidx - 1;
+      if (lane == 0 && G < gchunk) bm[G] = static_cast<uint16_t>((carry >> hd) & 0xffffu);
+      T += __reduce_add_sync(0xffffffffu, chunk_cnt);
+      if (Q >= 5) {
+        if (two && 2 * second > steps) single_left = 16;
+        else if (!two) --single_left;
+      }
+      __syncwarp();  // staging buffer st is free again
+      continue;
+    }
     // hot loop: the first stage of two steps at once (independent loads,
     // one vote for both); a step in which some lane has a candidate is
     // finished apart.  A step past the chunk's end tests nothing (all its
     // lanes are past the end).
-    for (int base = -a.head; base < wins; base += 1024) {
+    for (int base = -a.head, sidx = 0; base < wins; base += 1024, sidx += 2) {
       uint32_t Tw0[6], dg0[4], Tw1[6], dg1[4];
       const uint32_t c0 = test(base, Tw0, dg0);
       const uint32_t c1 = test(base + 512, Tw1, dg1);
       steps += 2;
       if (__any_sync(0xffffffffu, (c0 | c1) != 0u)) {
-        if (__any_sync(0xffffffffu, c0 != 0u)) finish_step(base, Tw0, dg0, c0);
-        if (__any_sync(0xffffffffu, c1 != 0u)) finish_step(base + 512, Tw1, dg1, c1);
+        const uint32_t cl0 = __ballot_sync(0xffffffffu, c0 != 0u);
+        const uint32_t cl1 = __ballot_sync(0xffffffffu, c1 != 0u);
+        const int n0 = __popc(cl0), n1 = __popc(cl1);
+        second += n0 + n1;
+        if (n0 >= kDirectLanes) {
+          finish_now(base, Tw0, dg0, c0);
+        } else if (n0 != 0) {
+          if (qn > kQueueCap - 32) flush();
+          enqueue(sidx, cl0);
+        }
+        if (n1 >= kDirectLanes) {
+          finish_now(base + 512, Tw1, dg1, c1);
+        } else if (n1 != 0) {
+          if (qn > kQueueCap - 32) flush();
+          enqueue(sidx + 1, cl1);
+        }
       }
     }
+    flush();  // before the staging buffer is released
     if (Q >= 5) {
-      if (two && 2 * second > steps) single_left = 16;
+      // the first stage pays while it leaves few candidate lanes per step
+      if (two && second > kTwoStageLanes * steps) single_left = 16;
       else if (!two) --single_left;
     }
     if (store && t > S) overflow = (static_cast<unsigned long long>(i) << 40) | T;
@@ -309,7 +422,7 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
   }
 }
 
-template <int Q>
+template <int Q, bool BM>
 __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
@@ -318,7 +431,7 @@ __global__ void __launch_bounds__(kThreads) hc_scan_dense_kernel(const SearchArg
   // kernel: nothing of memory is touched before that kernel has completed
   // (only the launch and the CTAs' start overlap its tail)
   pdl_wait();
-  dense_stream<Q>(a, smem, bars[threadIdx.x >> 5]);
+  dense_stream<Q, BM>(a, smem, bars[threadIdx.x >> 5]);
   block_total(a);
 }
 
@@ -355,16 +468,17 @@ KernelFn scan_kernel_for_q(int q) {
   }
 }
 
+template <bool BM>
 KernelFn dense_kernel_for_q(int q) {
   switch (q) {
-    case 1: return hc_scan_dense_kernel<1>;
-    case 2: return hc_scan_dense_kernel<2>;
-    case 3: return hc_scan_dense_kernel<3>;
-    case 4: return hc_scan_dense_kernel<4>;
-    case 5: return hc_scan_dense_kernel<5>;
-    case 6: return hc_scan_dense_kernel<6>;
-    case 7: return hc_scan_dense_kernel<7>;
-    default: return hc_scan_dense_kernel<8>;
+    case 1: return hc_scan_dense_kernel<1, BM>;
+    case 2: return hc_scan_dense_kernel<2, BM>;
+    case 3: return hc_scan_dense_kernel<3, BM>;
+    case 4: return hc_scan_dense_kernel<4, BM>;
+    case 5: return hc_scan_dense_kernel<5, BM>;
+    case 6: return hc_scan_dense_kernel<6, BM>;
+    case 7: return hc_scan_dense_kernel<7, BM>;
+    default: return hc_scan_dense_kernel<8, BM>;
   }
 }
 
@@ -525,16 +639,25 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   } else if (sp_opt == 1) {
     return set_error(HC_ERR_ARG, "hc_search: single_pass applies to the dense mode only");
   }
+  const int bm_opt = o ? o->bitmap : 0;
+  if (bm_opt < 0 || bm_opt > 1) return set_error(HC_ERR_ARG, "hc_search: bitmap must be 0 or 1");
+  if (bm_opt == 1 && p.single_pass)
+    return set_error(HC_ERR_ARG, "hc_search: the bitmap form and the single pass exclude each other");
   if (kind == HC_MODE_DENSE && !p.single_pass) {
     // one ring of `stages` buffers per warp
-    p.scan = dense_kernel_for_q(f->q);
-    p.smem_scan = size_t(kWarps) * stages * p.stage_bytes;  // F is not staged
+    p.bitmap = bm_opt == 1;
+    p.scan = p.bitmap ? dense_kernel_for_q<true>(f->q) : dense_kernel_for_q<false>(f->q);
+    // F is not staged; the spill form adds each warp's candidate queue
+    p.smem_scan = size_t(kWarps) * stages * p.stage_bytes + (p.bitmap ? 0 : size_t(kWarps) * kQueueCap * 2);
     if (mode == HC_MODE_AUTO && p.smem_scan + static_smem(p.scan) > di.smem_optin) {
       kind = HC_MODE_STAGED;  // caller's lane_bytes too large for per-warp rings
       p.C = 32u * static_cast<uint32_t>(L);
       p.stage_bytes = stage_bytes_for(p.C, f->m, false);
+      p.bitmap = false;
     }
   }
+  if (bm_opt == 1 && !p.bitmap)
+    return set_error(HC_ERR_ARG, "hc_search: the bitmap form applies to the dense mode only");
   p.kind = kind;
   const int sentinel = o ? o->sentinel : 0;
   if (sentinel < 0 || sentinel > 1) return set_error(HC_ERR_ARG, "hc_search: sentinel must be 0 or 1");
@@ -561,8 +684,8 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   }
   if (p.smem_scan + static_smem(p.scan) > di.smem_optin)
     return set_error(HC_ERR_ARG, "hc_search: filter and buffers exceed shared memory");
-  p.emit = emit_kernel_for_q(f->q);
-  p.smem_emit = (((f->F.size() + 3) & ~size_t(3)) * 4) + slot_bytes;
+  p.emit = p.bitmap ? emit_bitmap_kernel() : emit_kernel_for_q(f->q);
+  p.smem_emit = p.bitmap ? 0 : (((f->F.size() + 3) & ~size_t(3)) * 4) + slot_bytes;
   // warp-speculative HC only on request: measured on GB300 it loses to the
   // per-lane form on every sweep cell (each first-test hit serialises the
   // warp), so the automatic choice is the per-lane form
@@ -611,6 +734,17 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   p.records = (p.num_chunks + p.chunks_per_cta - 1) / p.chunks_per_cta;
   p.grid = (p.records + per_record - 1) / per_record;
   p.records = p.grid * per_record;
+  if (p.bitmap) {
+    // records' totals and overflow words, the CTAs' totals, then C / 8
+    // bytes of window bits per chunk; the emit kernel has one warp per record
+    p.region_entries = 0;
+    p.emit_group = 0;
+    p.emit_ctas = p.grid;
+    p.bitmap_bytes = p.num_chunks * (p.C / 8);
+    p.ws_bytes = ((p.records * 16 + p.grid * 8 + 15) & ~15ull) + p.bitmap_bytes;
+    *out = p;
+    return HC_OK;
+  }
   unsigned long long spill = o ? o->spill_entries : 0;
   if (spill == 0)
     spill = cap == 0 ? 0 : std::min<unsigned long long>(nwin, std::max<unsigned long long>(cap, 1ull << 20));
@@ -678,6 +812,8 @@ void fill_args(const Filter* f, const SearchPlan& p, const uint8_t* y, size_t n,
     a.region = reinterpret_cast<uint32_t*>(a.cta_overflow + p.records);
     // after the regions (R * S * 4 bytes, S a multiple of 4: 16-byte aligned)
     a.blk_total = reinterpret_cast<unsigned long long*>(a.region + p.records * p.region_entries);
+    if (p.bitmap)
+      a.bitmap = reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(ws) + ((p.records * 16 + p.grid * 8 + 15) & ~15ull));
   }
   a.region_entries = p.region_entries;
   a.num_chunks = p.num_chunks;
@@ -850,12 +986,13 @@ int hc_check_bounds(uint64_t* violations) {
   clear_error();
   if (violations == nullptr) return set_error(HC_ERR_ARG, "hc_check_bounds: violations is NULL");
   *violations = 0;
-  uint64_t a = 0, b = 0;
+  uint64_t a = 0, b = 0, c = 0;
   int rc = take_bound_violations_search(&a);
   if (rc == HC_ERR_STATE) return set_error(HC_ERR_STATE, "hc_check_bounds: not a checked build");
   if (rc == HC_OK) rc = take_bound_violations_batch(&b);
+  if (rc == HC_OK) rc = take_bound_violations_dense(&c);
   if (rc != HC_OK) return rc;
-  *violations = a + b;
+  *violations = a + b + c;
   return HC_OK;
 }
 

@@ -120,6 +120,7 @@ struct Server {
   std::deque<Text> texts;
   uint64_t text_bytes = 0;
   std::deque<Req*> pending;
+  uint64_t pending_text = 0;                // text bytes of the queued requests
   std::unordered_map<uint64_t, Req*> done;  // completed, not yet released
   std::deque<uint64_t> done_queue;          // completed, not yet polled
   std::vector<Slot> slots;
@@ -173,21 +174,31 @@ int grow_pinned(T** p, size_t* cap, size_t need, unsigned flags, const char* wha
 
 }  // namespace
 
+// Text bytes the next batch may take: max_batch_bytes while the queue is
+// short, so that a request that arrives behind a batch waits for little text;
+// an equal share of the queued text per stream once more than max_inflight
+// batches of that size wait, so that a backlog drains in few large batches
+// (a request in a backlog waits for the text ahead of it whatever the cut).
+static uint64_t batch_text_bound(uint64_t max_batch_bytes, uint64_t queued_text, int streams) {
+  return std::max<uint64_t>(max_batch_bytes, queued_text / static_cast<uint64_t>(std::max(streams, 1)));
+}
+
 // Takes the next batch from the queue (lock held): queue order, at most
-// max_batch requests and max_batch_bytes of text (a lone larger request
-// still forms a batch), admitted memory within the limit, the combined
-// shared-memory layout within one CTA.
+// max_batch requests and batch_text_bound bytes of text (a lone larger
+// request still forms a batch), admitted memory within the limit, the
+// combined shared-memory layout within one CTA.
 std::vector<Req*> Server::take_batch() {
   std::vector<Req*> b;
   BatchLayout lay{};
   const size_t optin = device_info(dev).smem_optin;
-  uint64_t text_bytes = 0;  // of the batch: bounded so that a backlog is cut into several
-                            // batches that run on several streams and finish one by one
+  const uint64_t bound = batch_text_bound(cfg.max_batch_bytes, pending_text, cfg.max_inflight);
+  uint64_t text_bytes = 0;  // of the batch
   while (!pending.empty() && b.size() < static_cast<size_t>(cfg.max_batch)) {
     Req* r = pending.front();
-    if (!b.empty() && text_bytes + r->n > cfg.max_batch_bytes) break;
+    if (!b.empty() && text_bytes + r->n > bound) break;
     if (r->dev_bytes > request_limit()) {  // can never be admitted
       pending.pop_front();
+      pending_text -= r->n;
       r->status = HC_ERR_ADMISSION;
       r->done_ns = now_ns();
       done[r->id] = r;
@@ -209,6 +220,7 @@ std::vector<Req*> Server::take_batch() {
     text_bytes += r->n;
     inflight_bytes += r->dev_bytes;
     pending.pop_front();
+    pending_text -= r->n;
   }
   st.peak_inflight_bytes = std::max(st.peak_inflight_bytes, inflight_bytes);
   return b;
@@ -529,6 +541,7 @@ void Server::run() {
     done_queue.push_back(r->id);
   }
   pending.clear();
+  pending_text = 0;
   cv_done.notify_all();
 }
 
@@ -742,6 +755,7 @@ void enqueue(Server* s, Req* r, uint64_t* id) {
     std::lock_guard<std::mutex> lock(s->mu);
     r->id = s->next_id++;
     s->pending.push_back(r);
+    s->pending_text += r->n;
     s->st.submitted++;
     *id = r->id;
   }

@@ -251,6 +251,7 @@ int time_candidate_single(Scratch& sc, int dev, const std::vector<uint8_t>& xh, 
   o.lane_bytes = p.lane_bytes;
   o.mode = p.mode;
   o.sentinel = p.sentinel;
+  o.bitmap = p.bitmap;
   SearchPlan sp;
   if (plan_search(f, n, 0, &o, dev, &sp) != HC_OK) {
     clear_error();
@@ -402,6 +403,29 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
       best_sentinel = 1;
     }
   }
+  // the bitmap form of the dense scan (single searches, m = q): kept where
+  // it is faster (patterns with many occurrences), at the lane width found
+  // above or twice or half of it
+  int best_bitmap = 0;
+  if (path == HC_TUNE_SINGLE && best_mode == HC_MODE_DENSE) {
+    const int Lb = best_L;
+    for (int L : {Lb, Lb * 2, Lb / 2}) {
+      if (L < 2 || L > 256) continue;
+      QueryParams p = bp;
+      p.lane_bytes = L;
+      p.mode = HC_MODE_DENSE;
+      p.bitmap = 1;
+      double s = INFINITY;
+      int Lr = 0, mr = 0;
+      int rc = time_it(p, n, 3, true, &s, &Lr, &mr);
+      if (rc != HC_OK) return rc;
+      if (s < best && mr == HC_MODE_DENSE) {
+        best = s;
+        best_bitmap = 1;
+        best_L = Lr;
+      }
+    }
+  }
   hc_tune_entry c{};
   c.sigma = sigma;
   c.m = m;
@@ -410,6 +434,7 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
   c.lane_bytes = best_L;
   c.mode = best_mode;
   c.sentinel = best_sentinel;
+  c.bitmap = best_bitmap;
   c.gbps = static_cast<double>(n) * kTunePatterns / best / 1e9;
   std::lock_guard<std::mutex> lock(t->mu);
   put_cell(t, c);
@@ -453,6 +478,7 @@ QueryParams tuner_lookup(const Tuner* t, double sigma, uint64_t m) {
   p.lane_bytes = best.lane_bytes;
   p.mode = best.mode;
   p.sentinel = best.sentinel;
+  p.bitmap = best.bitmap;
   if (best.m != m) {
     // launch options measured for another length: keep them only where they
     // still fit (the staged form's buffers grow with m; the dense form needs
@@ -462,6 +488,7 @@ QueryParams tuner_lookup(const Tuner* t, double sigma, uint64_t m) {
       p.mode = HC_MODE_AUTO;
       p.lane_bytes = 0;
       p.sentinel = 0;
+      p.bitmap = 0;
     }
   }
   return p;
@@ -555,6 +582,7 @@ int hc_tuner_lookup(const hc_tuner* tp, double sigma, uint64_t m, hc_tune_entry*
   out->lane_bytes = p.lane_bytes;
   out->mode = p.mode;
   out->sentinel = p.sentinel;
+  out->bitmap = p.bitmap;
   return HC_OK;
 }
 
@@ -582,10 +610,10 @@ int hc_tuner_save(const hc_tuner* tp, const char* path) {
   FILE* f = std::fopen(path, "w");
   if (f == nullptr) return set_error(HC_ERR_STATE, std::string("hc_tuner_save: cannot open ") + path);
   std::lock_guard<std::mutex> lock(t->mu);
-  std::fprintf(f, "# sigma m q alpha lane_bytes mode gbps sentinel\n");
+  std::fprintf(f, "# sigma m q alpha lane_bytes mode gbps sentinel bitmap\n");
   for (const auto& c : t->cells)
-    std::fprintf(f, "%d %llu %d %d %d %d %.3f %d\n", c.sigma, static_cast<unsigned long long>(c.m), c.q, c.alpha,
-                 c.lane_bytes, c.mode, c.gbps, c.sentinel);
+    std::fprintf(f, "%d %llu %d %d %d %d %.3f %d %d\n", c.sigma, static_cast<unsigned long long>(c.m), c.q, c.alpha,
+                 c.lane_bytes, c.mode, c.gbps, c.sentinel, c.bitmap);
   const bool ok = std::fclose(f) == 0;
   return ok ? HC_OK : set_error(HC_ERR_STATE, "hc_tuner_save: write failed");
 }
@@ -606,10 +634,12 @@ int hc_tuner_load(hc_tuner* tp, const char* path) {
     if (*s == '#' || *s == '\n' || *s == '\0') continue;
     hc_tune_entry c{};
     unsigned long long m = 0;
-    // the last column (sentinel form) is optional: 0 when absent
-    const int got_fields = std::sscanf(s, "%d %llu %d %d %d %d %lf %d", &c.sigma, &m, &c.q, &c.alpha,
-                                       &c.lane_bytes, &c.mode, &c.gbps, &c.sentinel);
+    // the last two columns (sentinel form, bitmap form) are optional: 0
+    // when absent
+    const int got_fields = std::sscanf(s, "%d %llu %d %d %d %d %lf %d %d", &c.sigma, &m, &c.q, &c.alpha,
+                                       &c.lane_bytes, &c.mode, &c.gbps, &c.sentinel, &c.bitmap);
     if (got_fields < 7 || c.sentinel < 0 || c.sentinel > 1 || (c.sentinel == 1 && c.mode != HC_MODE_STAGED) ||
+        c.bitmap < 0 || c.bitmap > 1 || (c.bitmap == 1 && c.mode != HC_MODE_DENSE) ||
         c.sigma < 1 || m < 1 || c.q < 1 || c.q > kMaxQ || static_cast<unsigned long long>(c.q) > m ||
         c.alpha < 1 || c.alpha > kMaxAlpha || c.lane_bytes < 0 || c.lane_bytes > 4096 ||
         (c.mode != HC_MODE_AUTO && c.mode != HC_MODE_STAGED && c.mode != HC_MODE_DIRECT &&

@@ -120,7 +120,8 @@ def test_stored_tuner_table_only_on_gb300():
     assert bench.stored_tuner_table("skewed", "NVIDIA GB300", False).endswith("tuner_skewed_gb300.txt")
     assert bench.stored_tuner_table("sweep", "NVIDIA B200", False) is None
     assert bench.stored_tuner_table("sweep", "NVIDIA GB300", True) is None
-    assert bench.stored_tuner_table("batched", "NVIDIA GB300", False) is None
+    assert bench.stored_tuner_table("batched", "NVIDIA GB300", False).endswith("tuner_batched_gb300.txt")
+    assert bench.stored_tuner_table("served", "NVIDIA GB300", False) is None
 
 
 def test_direct_cell_traffic_needs_the_same_launch(tmp_path, monkeypatch):

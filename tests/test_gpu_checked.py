@@ -78,23 +78,26 @@ def test_single_search_kinds_checked(hc):
         y_dev = ybuf[off:off + n]
         f = hc.hc_preprocess(x, q, alpha)
         modes = [0, 1, 2] + ([3] if m == q else [])
-        for mode in modes:
-            for spill in (0, 1):
-                for cap in (want.size + 2, max(1, want.size // 2)):
-                    pbuf, pos = _guarded(cap)
-                    cbuf, cnt = _guarded(1)
-                    try:
-                        hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(mode=mode, spill_entries=spill))
-                    except hc.HCError as e:       # staged buffers too large for this m
-                        assert e.code == hc.HC_ERR_ARG and mode == 1
-                        continue
-                    torch.cuda.synchronize()
-                    hc.hc_check_status()
-                    k = min(cap, want.size)
-                    assert int(cnt.item()) == want.size, (sigma, m, q, alpha, mode)
-                    assert np.array_equal(pos[:k].cpu().numpy().view(np.uint64), want[:k])
-                    assert _intact(pbuf, cap) and _intact(cbuf, 1), (sigma, m, mode, spill, cap)
-                    cases += 1
+        forms = [dict(mode=mode, spill_entries=spill) for mode in modes for spill in (0, 1)]
+        if m == q:
+            forms.append(dict(mode=3, bitmap=1, lane_bytes=int(rng.choice([2, 8, 16]))))
+        for form in forms:
+            mode = form["mode"]
+            for cap in (want.size + 2, max(1, want.size // 2)):
+                pbuf, pos = _guarded(cap)
+                cbuf, cnt = _guarded(1)
+                try:
+                    hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(**form))
+                except hc.HCError as e:       # staged buffers too large for this m
+                    assert e.code == hc.HC_ERR_ARG and mode == 1
+                    continue
+                torch.cuda.synchronize()
+                hc.hc_check_status()
+                k = min(cap, want.size)
+                assert int(cnt.item()) == want.size, (sigma, m, q, alpha, form)
+                assert np.array_equal(pos[:k].cpu().numpy().view(np.uint64), want[:k])
+                assert _intact(pbuf, cap) and _intact(cbuf, 1), (sigma, m, form, cap)
+                cases += 1
         f.free()
     assert cases > 200
     assert _violations(hc) == 0

@@ -278,6 +278,74 @@ def test_dense_single_pass_tiles_and_edges(opts):
         f.free()
 
 
+@pytest.mark.parametrize("opts", [
+    dict(bitmap=1), dict(bitmap=1, lane_bytes=2), dict(bitmap=1, lane_bytes=16),
+    dict(bitmap=1, lane_bytes=32, pos32=1), dict(bitmap=1, lane_bytes=40), dict(bitmap=1, lane_bytes=7),
+    dict(bitmap=1, pos32=1, stages=3),
+])
+def test_dense_bitmap_form(opts):
+    """The dense scan's bitmap form (one bit per window start, expanded by
+    its emit kernel): texts from one window to a few MB at every 16-byte
+    offset (the lanes' windows then straddle the bitmap's 16-window groups by
+    that many), every window a match (sigma = 1) and random texts, ragged
+    ends, capacities from 0 to above the count; the count is exact and the
+    first min(count, cap) positions equal the oracle's, nothing written past
+    them."""
+    hc = _hc()
+    rng = np.random.default_rng(977)
+    opts = dict(opts, mode=3)
+    pos32 = opts.get("pos32", 0) == 1
+    cases = [(1, 1, 1), (1, 3, 3), (2, 2, 2), (4, 4, 5), (1, 2, 511), (2, 1, 513), (4, 3, 4096),
+             (1, 4, 70_001), (2, 2, 1_000_003), (4, 5, 777_777), (20, 6, 300_000), (95, 8, 2_500_001),
+             (4, 7, 123_457), (3, 8, 600_000), (2, 1, 3_000_001), (1, 1, 1_048_577), (2, 3, 16_385)]
+    for i, (sigma, m, n) in enumerate(cases):
+        x, y = _case(rng, sigma, n, m, plant=int(rng.integers(0, 60)))
+        want = oracle.hc_search(x, y, m, 12)
+        offset = (i * 7) % 16
+        y_dev, keep = _upload(y, offset=offset)
+        f = hc.hc_preprocess(x, m, 12)
+        for cap in sorted({0, 1, want.size // 3, want.size, want.size + 2}):
+            dt = torch.int32 if pos32 else torch.int64
+            buf = torch.full((cap + 2,), -7, dtype=dt, device="cuda")
+            pos = buf[1:1 + cap] if cap else None
+            cnt = torch.full((1,), -5, dtype=torch.int64, device="cuda")
+            hc.hc_search_ex(f, y_dev, pos, cnt, hc.SearchOpts(**opts), cap=cap)
+            torch.cuda.synchronize()
+            hc.hc_check_status()
+            assert int(cnt.item()) == want.size, (sigma, m, n, offset, opts, cap)
+            k = min(cap, want.size)
+            got = buf.cpu().numpy()
+            vals = got[1:1 + k].view(np.uint32).astype(np.uint64) if pos32 else got[1:1 + k].view(np.uint64)
+            assert np.array_equal(vals, want[:k]), (sigma, m, n, offset, opts, cap)
+            assert got[0] == -7 and (got[1 + k:] == -7).all(), (sigma, m, n, offset, opts, cap)
+        f.free()
+
+
+def test_dense_bitmap_form_full_size():
+    """The bitmap form on the 256 MiB sigma = 2 sweep text, m = q = 2 (a
+    quarter of all windows are occurrences: 67 M positions, every emit round
+    full) and sigma = 4, m = q = 4, with u32 positions, against the oracle."""
+    hc = _hc()
+    for sigma, m in ((2, 2), (4, 4)):
+        y = hi.sweep_text(sigma)
+        x = hi.sweep_patterns(y, sigma, m, count=1)[0]
+        want = oracle.hc_search(x, y, m, 8)
+        y_dev = torch.from_numpy(y).cuda()
+        f = hc.hc_preprocess(x, m, 8)
+        pos = torch.full((want.size + 1,), -7, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        hc.hc_search_ex(f, y_dev, pos[:want.size], cnt, hc.SearchOpts(mode=3, bitmap=1, lane_bytes=16, pos32=1),
+                        cap=want.size)
+        torch.cuda.synchronize()
+        hc.hc_check_status()
+        assert int(cnt.item()) == want.size
+        got = pos.cpu().numpy()
+        assert np.array_equal(got[:want.size].view(np.uint32).astype(np.uint64), want)
+        assert got[want.size] == -7
+        f.free()
+        del y_dev
+
+
 @pytest.mark.parametrize("speculate", [1, -1])
 def test_speculative_and_per_lane_forms(speculate):
     """Both forms of the staged/direct scan against the oracle, for every q,
@@ -442,9 +510,16 @@ def test_search_opts_rejected_when_out_of_range():
     for bad in (dict(lane_bytes=5000), dict(stages=5), dict(stages=1), dict(mode=3),
                 dict(mode=7), dict(single_pass=2), dict(single_pass=-2), dict(tile_steps=65),
                 dict(tile_steps=-1), dict(mode=1, single_pass=1), dict(sentinel=2),
-                dict(mode=2, sentinel=1), dict(mode=3, sentinel=1)):
+                dict(mode=2, sentinel=1), dict(mode=3, sentinel=1), dict(bitmap=2), dict(bitmap=-1),
+                dict(bitmap=1), dict(mode=1, bitmap=1), dict(mode=2, bitmap=1)):
         with pytest.raises(hc.HCError) as ei:
             hc.hc_search_ex(f, y_dev, None, cnt, hc.SearchOpts(**bad))
+        assert ei.value.code == hc.HC_ERR_ARG
+    # m = q: the bitmap form excludes the single pass and needs the dense mode
+    f4 = hc.hc_preprocess(b"ACGT", 4, 12)
+    for bad in (dict(bitmap=1, single_pass=1), dict(mode=1, bitmap=1), dict(bitmap=1, lane_bytes=300)):
+        with pytest.raises(hc.HCError) as ei:
+            hc.hc_search_ex(f4, y_dev, None, cnt, hc.SearchOpts(**bad))
         assert ei.value.code == hc.HC_ERR_ARG
 
 

@@ -223,12 +223,23 @@ def test_bad_requests_rejected(hc):
     srv.destroy()
 
 
+def _batch_text(res, ys, rids, reqs):
+    text_of = dict(zip(rids, (ti for ti, _ in reqs)))
+    per_batch, size_of = {}, {}
+    for r in res:
+        per_batch[r["batch"]] = per_batch.get(r["batch"], 0) + ys[text_of[r["id"]]].size
+        size_of[r["batch"]] = r["batch_size"]
+    return per_batch, size_of
+
+
 def test_batches_bounded_by_text_bytes(hc):
-    """A backlog submitted at once is cut into batches of at most
-    max_batch_bytes of text (a single larger request runs alone), which run on
-    several streams; every result still equals the oracle's."""
-    bound = 2_000_000
-    srv = hc.HCServer(hc.ServerConfig(max_batch_bytes=bound, max_batch=64))
+    """Requests that arrive one by one form batches of at most max_batch_bytes
+    of text (a single larger request runs alone); a backlog submitted at once
+    is cut into batches of at most max(max_batch_bytes, queued text /
+    max_inflight) -- several batches, on several streams.  Every result still
+    equals the oracle's."""
+    bound, streams = 2_000_000, 3
+    srv = hc.HCServer(hc.ServerConfig(max_batch_bytes=bound, max_batch=64, max_inflight=streams))
     ys, ids = _texts(srv)
     rng = np.random.default_rng(77)
     reqs = _requests(ys, 120, rng)
@@ -237,12 +248,17 @@ def test_batches_bounded_by_text_bytes(hc):
     srv.drain()
     res = _collect(srv, len(reqs))
     _check(res, ys, dict(zip(rids, reqs)))
-    text_of = dict(zip(rids, (ti for ti, _ in reqs)))
-    per_batch, size_of = {}, {}
-    for r in res:
-        per_batch[r["batch"]] = per_batch.get(r["batch"], 0) + ys[text_of[r["id"]]].size
-        size_of[r["batch"]] = r["batch_size"]
-    assert all(v <= bound or size_of[b] == 1 for b, v in per_batch.items())
+    per_batch, size_of = _batch_text(res, ys, rids, reqs)
     total = sum(ys[ti].size for ti, _ in reqs)
-    assert len(per_batch) >= total // bound
+    assert all(v <= max(bound, total // streams) or size_of[b] == 1 for b, v in per_batch.items())
+    assert len(per_batch) >= streams
+    # arrivals spaced so that the queue stays short: the plain bound holds
+    reqs2 = _requests(ys, 40, rng)
+    rq2 = [(ids[ti], x) for ti, x in reqs2]
+    rids2 = srv.replay(rq2, [i * 2e-3 for i in range(len(rq2))])
+    srv.drain()
+    res2 = _collect(srv, len(reqs2))
+    _check(res2, ys, dict(zip(rids2, reqs2)))
+    per_batch, size_of = _batch_text(res2, ys, rids2, reqs2)
+    assert all(v <= bound or size_of[b] == 1 for b, v in per_batch.items())
     srv.destroy()

@@ -123,9 +123,32 @@ def test_sentinel_column_round_trips(hc, tmp_path):
     t2.free()
 
 
+def test_bitmap_column_round_trips(hc, tmp_path):
+    """The optional ninth column marks a dense (m = q) cell measured fastest
+    in the bitmap form; lookups return it at that m and drop it (with the
+    dense mode) at another m; files without it read 0."""
+    p = str(tmp_path / "b.txt")
+    _write(p, ["2 2 2 8 16 3 2.6 0 1", "4 4 4 8 16 3 2.8 0", "20 32 6 12 124 1 5.5"])
+    t = hc.HCTuner()
+    t.load(p)
+    assert t.lookup(2, 2)["bitmap"] == 1 and t.lookup(2, 2)["mode"] == 3
+    assert t.lookup(4, 4)["bitmap"] == 0 and t.lookup(20, 32)["bitmap"] == 0
+    far = t.lookup(2, 3)             # nearest cell is m = 2; q = 2 != 3, so no dense form
+    assert far["bitmap"] == 0 and far["mode"] == 0
+    q = str(tmp_path / "b2.txt")
+    t.save(q)
+    t2 = hc.HCTuner()
+    t2.load(q)
+    assert t2.entries() == t.entries()
+    assert t2.lookup(2, 2)["bitmap"] == 1
+    t.free()
+    t2.free()
+
+
 @pytest.mark.parametrize("bad", ["4 8 9 12 0 0 1", "4 8 4 16 0 0 1", "4 8 4 12 0 7 1", "4 8 4 12 0 3 1",
                                  "4 2 3 12 0 0 1", "0 8 4 12 0 0 1", "4 8 4 12 0 0",
-                                 "4 8 4 12 5000 0 1", "garbage", "4 8 4 12 0 2 1 1", "4 8 4 12 0 1 1 2"])
+                                 "4 8 4 12 5000 0 1", "garbage", "4 8 4 12 0 2 1 1", "4 8 4 12 0 1 1 2",
+                                 "4 4 4 12 0 3 1 0 2", "4 8 4 12 0 1 1 0 1", "4 4 4 12 0 3 1 1 1"])
 def test_malformed_lines_rejected(hc, tmp_path, bad):
     p = str(tmp_path / "bad.txt")
     _write(p, ["4 16 6 12 0 0 1", bad])
