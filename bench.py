@@ -280,7 +280,7 @@ def dense_single_pass(opts, m: int) -> bool:
     two tiles' step masks within the 227 KB of shared memory per block)."""
     if opts is None or getattr(opts, "single_pass", 0) != 1:
         return False
-    lane = opts.lane_bytes if opts is not None and opts.lane_bytes else 8
+    lane = opts.lane_bytes if opts is not None and opts.lane_bytes else 16
     stages = opts.stages if opts is not None and opts.stages else 2
     ls = max(2, (lane + 1) & ~1)
     spc = ls // 2

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(kThreads, 4) hc_scan_kernel(const SearchArgs a
 template <int Q, bool BM>
 __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem, uint64_t* wb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lanes_below = (1u << lane) - 1u;
   const unsigned long long w_id = static_cast<unsigned long long>(blockIdx.x) * kWarps + warp;
 
   const unsigned long long c0 = w_id * a.chunks_per_cta;
@@ -218,6 +219,20 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
       // nonzero iff some dg[g] has a zero byte (exact for the test; the flag
       // positions above a zero byte may be wrong, so they are not used)
       return (live && filter_passes) ? any_zero_byte4(dg) : 0u;
+    };
+    // The same for a step in which every lane's first window lies before
+    // the chunk's end (no liveness test, no clamp), used only where
+    // F[h(x)] != 0 and h(x) = H_v.
+    auto test_full = [&](int base, uint32_t (&Tw)[6], uint32_t (&dg)[4]) -> uint32_t {
+      const uint32_t o = static_cast<uint32_t>(a.head + base + 16 * lane);
+      HC_IN_BOUNDS(o + 24u <= a.stage_bytes);
+      const uint4 A = *reinterpret_cast<const uint4*>(sb + o);
+      const uint2 B = *reinterpret_cast<const uint2*>(sb + o + 16);
+      Tw[0] = A.x; Tw[1] = A.y; Tw[2] = A.z; Tw[3] = A.w; Tw[4] = B.x; Tw[5] = B.y;
+      dg[0] = dg[1] = dg[2] = dg[3] = 0u;
+      if (two) or_columns<Q, 1, 0, 0>(Tw, xrep, dg);
+      else or_columns<Q, 0, 0, 0>(Tw, xrep, dg);
+      return any_zero_byte4(dg);
     };
     // The steps' candidate lanes wait in the warp's queue (entry: step
     // index << 5 | lane, in step order, lanes in order within a step) and
@@ -375,28 +390,52 @@ __device__ __forceinline__ void dense_stream(const SearchArgs& a, uint8_t* smem,
     // one vote for both); a step in which some lane has a candidate is
     // finished apart.  A step past the chunk's end tests nothing (all its
     // lanes are past the end).
-    for (int base = -a.head, sidx = 0; base < wins; base += 1024, sidx += 2) {
-      uint32_t Tw0[6], dg0[4], Tw1[6], dg1[4];
-      const uint32_t c0 = test(base, Tw0, dg0);
-      const uint32_t c1 = test(base + 512, Tw1, dg1);
-      steps += 2;
-      if (__any_sync(0xffffffffu, (c0 | c1) != 0u)) {
-        const uint32_t cl0 = __ballot_sync(0xffffffffu, c0 != 0u);
-        const uint32_t cl1 = __ballot_sync(0xffffffffu, c1 != 0u);
-        const int n0 = __popc(cl0), n1 = __popc(cl1);
-        second += n0 + n1;
-        if (n0 >= kDirectLanes) {
-          finish_now(base, Tw0, dg0, c0);
-        } else if (n0 != 0) {
-          if (qn > kQueueCap - 32) flush();
-          enqueue(sidx, cl0);
-        }
-        if (n1 >= kDirectLanes) {
-          finish_now(base + 512, Tw1, dg1, c1);
-        } else if (n1 != 0) {
-          if (qn > kQueueCap - 32) flush();
-          enqueue(sidx + 1, cl1);
-        }
+    // the candidates of the step pair at `base` (step indexes sidx, sidx + 1)
+    auto handle = [&](int base, int sidx, uint32_t c0, uint32_t c1, const uint32_t (&Tw0)[6],
+                      uint32_t (&dg0)[4], const uint32_t (&Tw1)[6], uint32_t (&dg1)[4]) {
+      if (!__any_sync(0xffffffffu, (c0 | c1) != 0u)) return;
+      const uint32_t cl0 = __ballot_sync(0xffffffffu, c0 != 0u);
+      const uint32_t cl1 = __ballot_sync(0xffffffffu, c1 != 0u);
+      const int n0 = __popc(cl0), n1 = __popc(cl1);
+      second += n0 + n1;
+      if (n0 < kDirectLanes && n1 < kDirectLanes) {
+        // both steps into the queue
+        if (qn > kQueueCap - 64) flush();
+        if (c0 != 0u) queue[qn + __popc(cl0 & lanes_below)] = static_cast<uint16_t>((sidx << 5) | lane);
+        if (c1 != 0u) queue[qn + n0 + __popc(cl1 & lanes_below)] = static_cast<uint16_t>(((sidx + 1) << 5) | lane);
+        qn += n0 + n1;
+        return;
+      }
+      if (n0 >= kDirectLanes) {
+        finish_now(base, Tw0, dg0, c0);
+      } else if (n0 != 0) {
+        if (qn > kQueueCap - 32) flush();
+        enqueue(sidx, cl0);
+      }
+      if (n1 >= kDirectLanes) {
+        finish_now(base + 512, Tw1, dg1, c1);
+      } else if (n1 != 0) {
+        if (qn > kQueueCap - 32) flush();
+        enqueue(sidx + 1, cl1);
+      }
+    };
+    if (filter_passes) {
+      int base = -a.head, sidx = 0;
+      // step pairs whose windows all lie before the chunk's end
+      for (; base + 1024 <= wins; base += 1024, sidx += 2) {
+        uint32_t Tw0[6], dg0[4], Tw1[6], dg1[4];
+        const uint32_t c0 = test_full(base, Tw0, dg0);
+        const uint32_t c1 = test_full(base + 512, Tw1, dg1);
+        steps += 2;
+        handle(base, sidx, c0, c1, Tw0, dg0, Tw1, dg1);
+      }
+      // the last, partial pair (lanes past the end test nothing)
+      if (base < wins) {
+        uint32_t Tw0[6], dg0[4], Tw1[6], dg1[4];
+        const uint32_t c0 = test(base, Tw0, dg0);
+        const uint32_t c1 = test(base + 512, Tw1, dg1);
+        steps += 2;
+        handle(base, sidx, c0, c1, Tw0, dg0, Tw1, dg1);
       }
     }
     flush();  // before the staging buffer is released
@@ -572,7 +611,7 @@ int plan_search(const Filter* f, size_t n, size_t cap, const hc_search_opts* o, 
   int L = L_req;
   if (L == 0) {
     if (kind == HC_MODE_DENSE) {
-      L = 8;
+      L = 16;
     } else if (kind == HC_MODE_DIRECT) {
       L = std::min(4096, std::max(64, shift));
     } else {

@@ -99,6 +99,7 @@ struct Slot {
   uint64_t* res_dev = nullptr;  // its device address
   size_t res_cap = 0;           // bytes
   unsigned int* status = nullptr;  // pinned copy of the device status word after the batch
+  std::vector<void*> retired;      // outgrown pinned buffers (freed with the server)
   uint64_t admitted = 0;
   uint64_t batch = 0;
 };
@@ -157,10 +158,16 @@ BatchLayout layout_max(const BatchLayout& a, const BatchLayout& b) {
   return {std::max(a.f_bytes, b.f_bytes), std::max(a.x_bytes, b.x_bytes), std::max(a.ring_bytes, b.ring_bytes)};
 }
 
+// Grows a pinned host buffer to at least `need` bytes (by half again, in
+// 64 KiB units).  The old buffer is not freed here: cudaFreeHost waits for
+// the whole device, which would stall every request in flight; it goes to
+// `retired`, freed when the server is destroyed (growth by half keeps the
+// retired buffers below twice the final size).
 template <typename T>
-int grow_pinned(T** p, size_t* cap, size_t need, unsigned flags, const char* what) {
+int grow_pinned(T** p, size_t* cap, size_t need, unsigned flags, const char* what,
+                std::vector<void*>* retired) {
   if (need <= *cap && *p != nullptr) return HC_OK;
-  if (*p != nullptr) cudaFreeHost(*p);
+  if (*p != nullptr) retired->push_back(*p);
   *p = nullptr;
   *cap = 0;
   const size_t n = align_up(std::max<size_t>(need + need / 2, 1 << 16), 1 << 16);
@@ -252,7 +259,7 @@ int Server::launch(Slot& s, std::vector<Req*>& b) {
     entries += b[i]->cap;
   }
   int rc = grow_pinned(&s.res, &s.res_cap, entries * 8, cudaHostAllocMapped | cudaHostAllocPortable,
-                       "cudaHostAlloc(server results)");
+                       "cudaHostAlloc(server results)", &s.retired);
   if (rc == HC_OK) {
     void* d = nullptr;
     cudaError_t e = cudaHostGetDevicePointer(&d, s.res, 0);
@@ -335,7 +342,7 @@ int Server::launch_batched(Slot& s, const std::vector<size_t>& which) {
   const size_t o_f = table_end;
   const size_t o_ws = o_f + align_up(plan.filter_words * 4);
   const size_t total = o_ws + align_up(plan.ws_bytes);
-  rc = grow_pinned(&s.stage, &s.stage_cap, table_end, cudaHostAllocPortable, "cudaHostAlloc(server staging)");
+  rc = grow_pinned(&s.stage, &s.stage_cap, table_end, cudaHostAllocPortable, "cudaHostAlloc(server staging)", &s.retired);
   if (rc != HC_OK) return rc;
   void* blk = nullptr;
   e = cudaMallocFromPoolAsync(&blk, total, device_pool(dev), s.stream);
@@ -382,7 +389,7 @@ int Server::launch_plain(Slot& s, const std::vector<size_t>& which) {
     off += align_up(f->F.size() * 4 + r->x.size(), 16);
   }
   if (rc == HC_OK)
-    rc = grow_pinned(&s.stage_plain, &s.stage_plain_cap, off, cudaHostAllocPortable, "cudaHostAlloc(server staging)");
+    rc = grow_pinned(&s.stage_plain, &s.stage_plain_cap, off, cudaHostAllocPortable, "cudaHostAlloc(server staging)", &s.retired);
   void* fx = nullptr;
   if (rc == HC_OK) {
     cudaError_t e = cudaMallocFromPoolAsync(&fx, std::max<size_t>(off, 16), device_pool(dev), s.stream);
@@ -569,6 +576,7 @@ void destroy_server(Server* s) {
     if (sl.stage_plain) cudaFreeHost(sl.stage_plain);
     if (sl.res) cudaFreeHost(sl.res);
     if (sl.status) cudaFreeHost(sl.status);
+    for (void* v : sl.retired) cudaFreeHost(v);
   }
   for (Text& t : s->texts)
     if (t.owned) cudaFree(const_cast<uint8_t*>(t.y));
@@ -618,6 +626,23 @@ int hc_server_create(const hc_server_config* cfg_in, const hc_tuner* tuner, hc_s
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&sl.status), sizeof(unsigned int), cudaHostAllocPortable);
     if (e != cudaSuccess) break;
+    // pinned buffers sized up front for a full batch of requests with the
+    // default capacity (at most 64 MiB of results), the launch tables of a
+    // full batch and 16 single-search filters of 2^13 words, so that they
+    // rarely grow while requests are served
+    const size_t res0 = std::min<size_t>((size_t(cfg.max_batch) * (cfg.default_cap + 1)) * 8, size_t(64) << 20);
+    int rc0 = grow_pinned(&sl.res, &sl.res_cap, res0, cudaHostAllocMapped | cudaHostAllocPortable,
+                          "cudaHostAlloc(server results)", &sl.retired);
+    if (rc0 == HC_OK)
+      rc0 = grow_pinned(&sl.stage, &sl.stage_cap, size_t(cfg.max_batch) * 1024, cudaHostAllocPortable,
+                        "cudaHostAlloc(server staging)", &sl.retired);
+    if (rc0 == HC_OK)
+      rc0 = grow_pinned(&sl.stage_plain, &sl.stage_plain_cap, size_t(16) * ((size_t(1) << 13) * 4 + 4096),
+                        cudaHostAllocPortable, "cudaHostAlloc(server staging)", &sl.retired);
+    if (rc0 != HC_OK) {
+      e = cudaErrorMemoryAllocation;
+      break;
+    }
   }
   if (e != cudaSuccess || status_word() == nullptr) {
     const int rc = e != cudaSuccess ? cuda_error(e, "hc_server_create") : set_error(HC_ERR_CUDA, "device status word unavailable");

@@ -370,8 +370,9 @@ int calibrate_cell(Tuner* t, Scratch& sc, int dev, const uint8_t* y, uint64_t n,
   if (!std::isfinite(best)) return set_error(HC_ERR_ARG, "hc_tuner_calibrate: no candidate fits");
   const int L0 = best_L;
   for (int mode : {HC_MODE_STAGED, HC_MODE_DIRECT, HC_MODE_DENSE})
-    for (int L : {L0 / 2, L0, L0 * 2}) {
+    for (int L : {L0 / 2, L0, L0 * 3 / 2, L0 * 2}) {
       if (L < 1 || L > 4096 || (mode == best_mode && L == L0)) continue;
+      if (L == L0 * 3 / 2 && mode != HC_MODE_DENSE) continue;  // wider dense lanes: fewer CTAs, larger steps
       if (mode == HC_MODE_DENSE && (path != HC_TUNE_SINGLE || static_cast<uint64_t>(bp.q) != m)) continue;
       QueryParams p = bp;
       p.lane_bytes = L;
