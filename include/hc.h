@@ -386,9 +386,9 @@ int hc_check_bounds(uint64_t *violations);
  *
  * plain = 1 runs each request as one plain search launch (host-built filter,
  * the kernels of hc_search_async) instead: the comparison form.  Otherwise
- * a batch's lone request, and in batches of at most 16 the requests with
- * m = q (served best by the dense single-search kernel), run that way too,
- * unless batch_only = 1.
+ * the requests of a batch of at most 3, and in batches of at most 16 the
+ * requests with m = q (served best by the dense single-search kernel), run
+ * that way too, unless batch_only = 1.
  */
 typedef struct hc_server hc_server;
 
@@ -400,8 +400,9 @@ typedef struct hc_server_config {
     uint64_t default_cap;   /* positions kept per request when its cap is 0; 0 = 4096 */
     int plain;              /* 1: one plain search launch per request */
     int batch_only;         /* 1: every request runs the batched kernels (0:
-                               a lone request, and m = q requests in batches
-                               of <= 16, run the single-search kernels) */
+                               batches of <= 3 requests, and m = q requests
+                               in batches of <= 16, run the single-search
+                               kernels) */
     uint64_t max_batch_bytes; /* text bytes per batch while the queue is
                                short (a single larger request still runs,
                                alone), so that a request arriving behind a

@@ -536,37 +536,21 @@ __device__ __forceinline__ int scan_segment(const uint8_t* base, int head, int l
   return cnt;
 }
 
-// Copies `words` 32-bit words (F) from global to shared memory, each thread
-// issuing up to eight loads before its stores (one round of memory latency
-// per 32 KB instead of one per 1 KB): 16-byte loads when both pointers are
-// 16-byte aligned and `words` is a multiple of 4, else 4-byte loads.  Every
-// thread of the CTA calls it; the caller synchronises before reading dst.
+// Copies `words` 32-bit words (F) from global to shared memory: 16-byte
+// loads when both pointers are 16-byte aligned and `words` is a multiple of
+// 4, else 4-byte loads.  (Keeping several loads of a thread in flight cost
+// registers -- the batched scan kernel went from 64 to 128 -- and measured
+// no faster: the copy overlaps the previous kernel's tail.)  Every thread of
+// the CTA calls it; the caller synchronises before reading dst.
 __device__ __forceinline__ void stage_words(uint32_t* dst, const uint32_t* src, uint32_t words) {
   const uint32_t tid = threadIdx.x;
   if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 && (words & 3u) == 0) {
     const uint4* s4 = reinterpret_cast<const uint4*>(src);
     uint4* d4 = reinterpret_cast<uint4*>(dst);
-    const uint32_t n4 = words >> 2;
-    for (uint32_t i0 = tid; i0 < n4; i0 += 8u * kThreads) {
-      uint4 v[8];
-#pragma unroll
-      for (uint32_t u = 0; u < 8; ++u)
-        if (i0 + u * kThreads < n4) v[u] = __ldg(s4 + i0 + u * kThreads);
-#pragma unroll
-      for (uint32_t u = 0; u < 8; ++u)
-        if (i0 + u * kThreads < n4) d4[i0 + u * kThreads] = v[u];
-    }
+    for (uint32_t i = tid; i < (words >> 2); i += kThreads) d4[i] = __ldg(s4 + i);
     return;
   }
-  for (uint32_t i0 = tid; i0 < words; i0 += 8u * kThreads) {
-    uint32_t v[8];
-#pragma unroll
-    for (uint32_t u = 0; u < 8; ++u)
-      if (i0 + u * kThreads < words) v[u] = __ldg(src + i0 + u * kThreads);
-#pragma unroll
-    for (uint32_t u = 0; u < 8; ++u)
-      if (i0 + u * kThreads < words) dst[i0 + u * kThreads] = v[u];
-  }
+  for (uint32_t i = tid; i < words; i += kThreads) dst[i] = __ldg(src + i);
 }
 
 // Copies n bytes (the pattern x) from global to shared memory: 16-byte loads

@@ -48,6 +48,7 @@ namespace {
 constexpr uint32_t kServerMagic = 0x48435356u;  // "HCSV"
 constexpr size_t kAlign = 256;
 constexpr size_t kSoloDenseMax = 16;  // batches up to this size route m = q requests to single searches
+constexpr size_t kSoloMax = 3;        // batches up to this size run every request as a single search
 
 size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
@@ -267,16 +268,19 @@ int Server::launch(Slot& s, std::vector<Req*>& b) {
     s.res_dev = static_cast<uint64_t*>(d);
   }
   if (rc != HC_OK) return rc;
-  // routing: in a small batch, m = q requests (one q-gram per window: the
-  // dense single-search kernel) run the single-search kernels, and so does a
-  // batch's lone request; the rest run the batched kernels.  In a large batch
-  // (a backlog) the per-launch host cost of the single searches would cost
-  // more than the dense kernel saves.
+  // routing: a batch of at most kSoloMax requests runs the single-search
+  // kernels (at low load the batched kernels' table setup and three launches
+  // only add latency); in a batch of at most kSoloDenseMax, m = q requests
+  // (one q-gram per window: the dense single-search kernel) run the
+  // single-search kernels, and so does a batch's lone request; the rest run
+  // the batched kernels.  In a large batch (a backlog) the per-launch host
+  // cost of the single searches would cost more than the dense kernel saves.
   std::vector<size_t> solo, batched;
   const bool route_dense = !cfg.batch_only && nq <= kSoloDenseMax;
+  const bool all_solo = !cfg.batch_only && nq <= kSoloMax;
   for (size_t i = 0; i < nq; ++i) {
     const bool dense = b[i]->x.size() == static_cast<size_t>(b[i]->p.q);
-    if (cfg.plain || (route_dense && dense)) solo.push_back(i);
+    if (cfg.plain || all_solo || (route_dense && dense)) solo.push_back(i);
     else batched.push_back(i);
   }
   if (!cfg.batch_only && batched.size() == 1) {
