@@ -823,10 +823,15 @@ def run_batched(args, rank, world, local_rank):
     tune_s = time.perf_counter() - t0
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
+    launches_per_run = {}
+
     def time_batch(b):
+        l0 = hc.hc_kernel_launches()
         with torch.cuda.stream(stream):
             b.run(stream=stream)
         stream.synchronize()
+        # preprocessing, one scan per occupancy class of the batch, emit
+        launches_per_run[id(b)] = hc.hc_kernel_launches() - l0
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             b.run(stream=stream)
@@ -921,8 +926,8 @@ def run_batched(args, rank, world, local_rank):
         "tune_s": round(tune_s, 2),
         "tuner": tuner.entries(),
         "batch_info": bt.info(),
-        "gpu_launches_per_step": 3,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches_per_step": launches_per_run[id(bt)],
+        "gpu_launches": launches_per_run[id(bt)] * args.steps,
         "library_launches_total": hc.hc_kernel_launches() - launches0,
         "clocks": clocks,
     }
