@@ -135,6 +135,18 @@ __device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v) {
   return v;
 }
 
+// Exclusive prefix sum over the lanes of a warp (all 32 lanes call it).
+__device__ __forceinline__ unsigned long long warp_excl_scan_u64(unsigned long long v) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long o = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += o;
+  }
+  return x - v;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);

@@ -775,6 +775,14 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
   const unsigned long long r1 = min(r0 + a.emit_group, a.records);
 
   __shared__ unsigned long long s_tot[kMaxEmitGroup], s_ovf[kMaxEmitGroup];
+  const int nrec = static_cast<int>(r1 - r0);
+  // the group's own records first: independent of the prefix loads below,
+  // so both rounds of loads are in flight together
+  unsigned long long my_tot = 0, my_ovf = kNoOverflow;
+  if (tid < nrec) {
+    my_tot = a.cta_total[r0 + tid];
+    my_ovf = a.cta_overflow[r0 + tid];
+  }
   unsigned long long p = 0;
   if (a.blk_total != nullptr) {
     // sum of the earlier records' totals: the CTAs wholly before record r0
@@ -797,32 +805,47 @@ __device__ __forceinline__ void emit_group(const SearchArgs& a, unsigned long lo
   }
   p = warp_sum_u64(p);
   if (lane == 0) red[warp] = p;
-  if (static_cast<unsigned long long>(tid) < r1 - r0) {
-    s_tot[tid] = a.cta_total[r0 + tid];
-    s_ovf[tid] = a.cta_overflow[r0 + tid];
+  if (tid < nrec) {
+    s_tot[tid] = my_tot;
+    s_ovf[tid] = my_ovf;
   }
   __syncthreads();
   // per record of the group: output offset P, positions to copy, and the
   // prefix of 2-position units, so that the whole group is copied in one
-  // pass (no per-record latency chain)
+  // pass (no per-record latency chain); warp 0, two records per lane, two
+  // warp scans
   __shared__ unsigned long long s_P[kMaxEmitGroup + 1], s_U[kMaxEmitGroup + 1], s_N[kMaxEmitGroup];
-  const int nrec = static_cast<int>(r1 - r0);
-  if (tid == 0) {
-    unsigned long long P = 0, U = 0;
-    for (int w = 0; w < kWarps; ++w) P += red[w];
-    for (int k = 0; k < nrec; ++k) {
-      const unsigned long long T = s_tot[k], ovf = s_ovf[k];
-      const unsigned long long stored = ovf == kNoOverflow ? T : (ovf & ((1ull << 40) - 1));
-      const unsigned long long ncopy = a.cap > P ? min(stored, a.cap - P) : 0ull;
-      s_P[k] = P;
-      s_U[k] = U;
-      s_N[k] = ncopy;
-      U += (ncopy + 1) / 2;
-      P += T;
+  if (warp == 0) {
+    unsigned long long P0 = 0;
+    for (int w = 0; w < kWarps; ++w) P0 += red[w];
+    const int k0 = 2 * lane, k1 = 2 * lane + 1;
+    auto stored_of = [&](int k) -> unsigned long long {
+      if (k >= nrec) return 0ull;
+      const unsigned long long ovf = s_ovf[k];
+      return ovf == kNoOverflow ? s_tot[k] : (ovf & ((1ull << 40) - 1));
+    };
+    const unsigned long long T0 = k0 < nrec ? s_tot[k0] : 0ull, T1 = k1 < nrec ? s_tot[k1] : 0ull;
+    const unsigned long long Pk0 = P0 + warp_excl_scan_u64(T0 + T1), Pk1 = Pk0 + T0;
+    const unsigned long long n0 = a.cap > Pk0 ? min(stored_of(k0), a.cap - Pk0) : 0ull;
+    const unsigned long long n1 = a.cap > Pk1 ? min(stored_of(k1), a.cap - Pk1) : 0ull;
+    const unsigned long long u0 = (n0 + 1) / 2, u1 = (n1 + 1) / 2;
+    const unsigned long long Uk0 = warp_excl_scan_u64(u0 + u1), Uk1 = Uk0 + u0;
+    if (k0 < nrec) {
+      s_P[k0] = Pk0;
+      s_U[k0] = Uk0;
+      s_N[k0] = n0;
     }
-    s_P[nrec] = P;
-    s_U[nrec] = U;
-    if (part == 0 && r1 == a.records) *a.count_out = P;
+    if (k1 < nrec) {
+      s_P[k1] = Pk1;
+      s_U[k1] = Uk1;
+      s_N[k1] = n1;
+    }
+    const unsigned long long Ptot = P0 + warp_sum_u64(T0 + T1), Utot = warp_sum_u64(u0 + u1);
+    if (lane == 0) {
+      s_P[nrec] = Ptot;
+      s_U[nrec] = Utot;
+      if (part == 0 && r1 == a.records) *a.count_out = Ptot;
+    }
   }
   __syncthreads();
   {

@@ -436,6 +436,67 @@ def test_outputs_in_mapped_host_memory(mode):
     f.free()
 
 
+def test_graph_captured_host_copies_and_searches():
+    """The end-to-end usage: per text a copy from pinned host memory into one
+    device buffer, then searches of every kernel kind (the dense bitmap form
+    too) writing positions and counts into mapped host memory, all captured
+    once in a CUDA graph and replayed twice with new host texts of the same
+    sizes; every replay's counts and last positions equal the oracle's."""
+    hc = _hc()
+    rng = np.random.default_rng(515)
+    specs = [(4, 9, 4, dict(mode=1)), (20, 700, 5, dict(mode=2)), (2, 3, 3, dict(mode=3)),
+             (4, 2, 2, dict(mode=3, bitmap=1))]
+    n = 3_000_017
+    pinned = torch.empty(n, dtype=torch.uint8).pin_memory()
+    y_dev = torch.empty(n + 16, dtype=torch.uint8, device="cuda")[3:3 + n]
+    cap = 1 << 21
+    pos = hc.MappedBuffer(cap)
+    cnt = hc.MappedBuffer(len(specs))
+    stream = torch.cuda.Stream()
+    filters = []
+    for sigma, m, q, opts in specs:
+        x = (rng.integers(0, sigma, m, dtype=np.uint16) + 65).astype(np.uint8)
+        f = hc.hc_preprocess(x, q, 11)
+        f.to_device()
+        filters.append((x, q, f, opts))
+
+    def step():
+        y_dev.copy_(pinned, non_blocking=True)
+        for i, (x, q, f, opts) in enumerate(filters):
+            hc.hc_search_ex(f, y_dev, pos.view(), cnt.view(i, 1), hc.SearchOpts(**opts), cap=cap, stream=stream)
+
+    with torch.cuda.stream(stream):
+        step()                                   # eager once (filters on the device, pool warm)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        step()
+    for rep in range(2):
+        y = (rng.integers(0, 4, n, dtype=np.uint16) + 65).astype(np.uint8)
+        for x, q, f, opts in filters:            # plant every pattern a few times
+            for _ in range(7):
+                off = int(rng.integers(0, n - x.size + 1))
+                y[off:off + x.size] = x
+        pinned.copy_(torch.from_numpy(y))
+        cnt.array()[:] = -1
+        with torch.cuda.stream(stream):
+            g.replay()
+        stream.synchronize()
+        hc.hc_check_status(stream)
+        for i, (x, q, f, opts) in enumerate(filters):
+            want = oracle.hc_search(x, y, q, 11)
+            assert int(cnt.array()[i]) == want.size, (rep, i)
+        x, q, f, opts = filters[-1]              # the positions buffer holds the last search's
+        want = oracle.hc_search(x, y, q, 11)
+        k = min(want.size, cap)
+        assert np.array_equal(pos.array()[:k].view(np.uint64), want[:k]), rep
+    del g
+    for _, _, f, _ in filters:
+        f.free()
+    pos.free()
+    cnt.free()
+
+
 @pytest.mark.parametrize("opts", [dict(pos32=1), dict(pos32=1, mode=1), dict(pos32=1, mode=2),
                                   dict(pos32=1, spill_entries=1), dict(pos32=1, mode=2, spill_entries=3)])
 def test_uint32_positions(opts):
