@@ -222,8 +222,10 @@ int hc_search(const hc_filter *f, const uint8_t *x, const uint8_t *y_dev,
  * tiles, and the output of positions and counts.  Runs on the same batch
  * must not overlap on the GPU.  q and alpha are per query; lane_bytes and
  * mode (HC_MODE_AUTO, _STAGED or _DIRECT; m = q runs in the staged form) are
- * launch options, 0 = automatic.  A query with q = 0 takes q, alpha and the
- * launch options from the autotuner given to hc_batch_create_tuned (from the
+ * launch options, 0 = automatic.  A query with q = 0 takes q and alpha
+ * (its launch options stay automatic: the tuner measures those on one query
+ * alone, and in a batch of mixed queries the automatic ones ran faster)
+ * from the autotuner given to hc_batch_create_tuned (from the
  * paper's Tables 1-3 without one) for its text's alphabet size: `sigma`, or
  * when sigma = 0 the effective alphabet size 1 / sum(p_c^2) of the byte
  * frequencies of a sample of the text, measured on the device at creation

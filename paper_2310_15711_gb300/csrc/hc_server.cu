@@ -742,8 +742,10 @@ int make_request(Server* s, const hc_server_request& q, uint64_t submit_ns, Req*
   const uint64_t nwin = t.n >= q.m ? t.n - q.m + 1 : 0;
   r->cap = std::min<uint64_t>(q.cap ? q.cap : s->cfg.default_cap, nwin);
   if (q.q == 0) {
-    r->p = tuner_lookup(s->tuner, t.sigma, q.m);
-    if (r->p.mode == HC_MODE_DENSE) r->p.mode = HC_MODE_AUTO;  // batched kernels have no dense form
+    // q and alpha from the tuner; launch options automatic, as in a batch
+    const QueryParams tp = tuner_lookup(s->tuner, t.sigma, q.m);
+    r->p.q = tp.q;
+    r->p.alpha = tp.alpha;
   } else {
     r->p.q = q.q;
     r->p.alpha = q.alpha;
