@@ -477,7 +477,10 @@ constexpr int kBitmapRound = 1024;  // windows per round (32 lanes x 32 bits)
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 4) hc_emit_bitmap_kernel(const SearchArgs a) {
-  __shared__ uint32_t s_buf[kWarps][kBitmapRound];
+  // per warp: a round's window starts, from slot `ph` on (ph < 4: the
+  // output's misalignment, so that buffer slot i pairs with an output
+  // element of the same 16-byte alignment)
+  __shared__ __align__(16) uint32_t s_buf[kWarps][kBitmapRound + 4];
   __shared__ unsigned long long s_red[kWarps];
   pdl_launch_dependents();  // the next search's scan may be scheduled; it waits for this grid
   pdl_wait();               // the scan grid has completed: its bits and totals are visible
@@ -524,21 +527,46 @@ __global__ void __launch_bounds__(kThreads, 4) hc_emit_bitmap_kernel(const Searc
       // window of this lane's bit 0, counted from W0 (< 2^32: a record's
       // windows are fewer than 2^32)
       const uint32_t rel = static_cast<uint32_t>(w - W0) + static_cast<uint32_t>(u * 32 + lane) * 32u;
-      uint32_t o = incl - cnt, b = v[u];
+      // output element P + j goes to buffer slot ph + j, where ph aligns
+      // the slots with the output's 16-byte blocks (4 u32 or 2 u64 each)
+      const uintptr_t oaddr = reinterpret_cast<uintptr_t>(a.pos);
+      const uint32_t ph = a.pos32 ? static_cast<uint32_t>(((oaddr >> 2) + P) & 3u)
+                                  : static_cast<uint32_t>(((oaddr >> 3) + P) & 1u);
+      uint32_t o = ph + incl - cnt, b = v[u];
       while (b) {
-        if (HC_IN_BOUNDS(o < static_cast<uint32_t>(kBitmapRound))) buf[o] = rel + static_cast<uint32_t>(__ffs(b) - 1);
+        if (HC_IN_BOUNDS(o < static_cast<uint32_t>(kBitmapRound + 4))) buf[o] = rel + static_cast<uint32_t>(__ffs(b) - 1);
         ++o;
         b &= b - 1u;
       }
       __syncwarp();
       const uint32_t lim = static_cast<uint32_t>(min(static_cast<unsigned long long>(tot), end - P));
+      const uint32_t last = ph + lim;  // slots [ph, last) are written out
       if (a.pos32) {
-        uint32_t* out = reinterpret_cast<uint32_t*>(a.pos) + P;
+        // 16-byte stores of four positions where a block lies inside
+        // [ph, last), 4-byte stores at the two ends
+        uint32_t* out = reinterpret_cast<uint32_t*>(a.pos);
         const uint32_t b32 = static_cast<uint32_t>(W0);
-        for (uint32_t i = lane; i < lim; i += 32) out[i] = b32 + buf[i];
+        for (uint32_t k = lane; 4 * k < last; k += 32) {
+          const uint32_t i0 = 4 * k;
+          if (i0 >= ph && i0 + 4 <= last) {
+            uint4 w = *reinterpret_cast<const uint4*>(buf + i0);
+            w.x += b32; w.y += b32; w.z += b32; w.w += b32;
+            *reinterpret_cast<uint4*>(out + (P + i0 - ph)) = w;
+          } else {
+            for (uint32_t i = max(i0, ph); i < min(i0 + 4, last); ++i) out[P + i - ph] = b32 + buf[i];
+          }
+        }
       } else {
-        unsigned long long* out = a.pos + P;
-        for (uint32_t i = lane; i < lim; i += 32) out[i] = W0 + buf[i];
+        unsigned long long* out = a.pos;
+        for (uint32_t k = lane; 2 * k < last; k += 32) {
+          const uint32_t i0 = 2 * k;
+          if (i0 >= ph && i0 + 2 <= last) {
+            const uint2 w = *reinterpret_cast<const uint2*>(buf + i0);
+            *reinterpret_cast<ulonglong2*>(out + (P + i0 - ph)) = make_ulonglong2(W0 + w.x, W0 + w.y);
+          } else {
+            for (uint32_t i = max(i0, ph); i < min(i0 + 2, last); ++i) out[P + i - ph] = W0 + buf[i];
+          }
+        }
       }
       __syncwarp();  // the buffer is free again
       P += tot;
