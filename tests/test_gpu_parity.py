@@ -297,7 +297,8 @@ def test_dense_bitmap_form(opts):
     pos32 = opts.get("pos32", 0) == 1
     cases = [(1, 1, 1), (1, 3, 3), (2, 2, 2), (4, 4, 5), (1, 2, 511), (2, 1, 513), (4, 3, 4096),
              (1, 4, 70_001), (2, 2, 1_000_003), (4, 5, 777_777), (20, 6, 300_000), (95, 8, 2_500_001),
-             (4, 7, 123_457), (3, 8, 600_000), (2, 1, 3_000_001), (1, 1, 1_048_577), (2, 3, 16_385)]
+             (4, 7, 123_457), (3, 8, 600_000), (2, 1, 3_000_001), (1, 1, 1_048_577), (2, 3, 16_385),
+             (2, 2, 40_000_003)]
     for i, (sigma, m, n) in enumerate(cases):
         x, y = _case(rng, sigma, n, m, plant=int(rng.integers(0, 60)))
         want = oracle.hc_search(x, y, m, 12)
@@ -324,7 +325,9 @@ def test_dense_bitmap_form(opts):
 def test_dense_bitmap_form_full_size():
     """The bitmap form on the 256 MiB sigma = 2 sweep text, m = q = 2 (a
     quarter of all windows are occurrences: 67 M positions, every emit round
-    full) and sigma = 4, m = q = 4, with u32 positions, against the oracle."""
+    full) and sigma = 4, m = q = 4, with u32 positions, against the oracle;
+    the capacity once the whole count and once about a third of it (the cut
+    then falls inside some record's chunks)."""
     hc = _hc()
     for sigma, m in ((2, 2), (4, 4)):
         y = hi.sweep_text(sigma)
@@ -332,16 +335,17 @@ def test_dense_bitmap_form_full_size():
         want = oracle.hc_search(x, y, m, 8)
         y_dev = torch.from_numpy(y).cuda()
         f = hc.hc_preprocess(x, m, 8)
-        pos = torch.full((want.size + 1,), -7, dtype=torch.int32, device="cuda")
-        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-        hc.hc_search_ex(f, y_dev, pos[:want.size], cnt, hc.SearchOpts(mode=3, bitmap=1, lane_bytes=16, pos32=1),
-                        cap=want.size)
-        torch.cuda.synchronize()
-        hc.hc_check_status()
-        assert int(cnt.item()) == want.size
-        got = pos.cpu().numpy()
-        assert np.array_equal(got[:want.size].view(np.uint32).astype(np.uint64), want)
-        assert got[want.size] == -7
+        for cap in (want.size, want.size // 3 + 5):
+            pos = torch.full((cap + 1,), -7, dtype=torch.int32, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            hc.hc_search_ex(f, y_dev, pos[:cap], cnt, hc.SearchOpts(mode=3, bitmap=1, lane_bytes=16, pos32=1),
+                            cap=cap)
+            torch.cuda.synchronize()
+            hc.hc_check_status()
+            assert int(cnt.item()) == want.size
+            got = pos.cpu().numpy()
+            assert np.array_equal(got[:cap].view(np.uint32).astype(np.uint64), want[:cap])
+            assert got[cap] == -7
         f.free()
         del y_dev
 
