@@ -463,8 +463,9 @@ KernelFn single_pass_init_kernel() { return hc_single_pass_init_kernel; }
 // output offset is the sum of the totals before it: one total per earlier
 // CTA of the scan (blk_total) plus the earlier warps of its own CTA.  It then
 // walks the record's bits in text order, 1024 windows per round (one 32-bit
-// word per lane; the words of kBitmapWords rounds are loaded at once, and a
-// round without a set bit costs one vote): a warp scan of the words'
+// word per lane; the words of kBitmapWords rounds are loaded at once, those
+// of the next kBitmapWords rounds requested before these run, and a round
+// without a set bit costs one vote): a warp scan of the words'
 // popcounts gives each lane its first slot, the lane writes its window
 // starts into the warp's shared-memory buffer in order, and the warp copies
 // the buffer to the output with consecutive stores.  (Splitting a record's
@@ -505,18 +506,30 @@ __global__ void __launch_bounds__(kThreads, 4) hc_emit_bitmap_kernel(const Searc
   const unsigned long long end = min(P + T, a.cap);    // output slots of this record
   const uint32_t* bits = reinterpret_cast<const uint32_t*>(a.bitmap);
   uint32_t* buf = s_buf[warp];
-  for (unsigned long long w = W0; w < W1 && P < end; w += static_cast<unsigned long long>(kBitmapRound) * kBitmapWords) {
+  const unsigned long long step = static_cast<unsigned long long>(kBitmapRound) * kBitmapWords;
+  // the lane's words of the kBitmapWords rounds from window w on (0 past W1)
+  auto load_block = [&](unsigned long long w, uint32_t (&dst)[kBitmapWords]) {
+#pragma unroll
+    for (int u = 0; u < kBitmapWords; ++u) {
+      const unsigned long long wl = w + static_cast<unsigned long long>(u * 32 + lane) * 32;
+      dst[u] = 0u;
+      if (wl < W1 && HC_IN_BOUNDS(wl / 32 < a.num_chunks * (a.C / 32))) dst[u] = __ldcs(bits + wl / 32);
+    }
+  };
+  uint32_t nv[kBitmapWords];
+  load_block(W0, nv);
+  for (unsigned long long w = W0; w < W1 && P < end; w += step) {
     uint32_t v[kBitmapWords];
+#pragma unroll
+    for (int u = 0; u < kBitmapWords; ++u) v[u] = nv[u];
+    // the next block's words are requested before this block's rounds run
+    if (w + step < W1) load_block(w + step, nv);
 #pragma unroll
     for (int u = 0; u < kBitmapWords; ++u) {
       // bits of windows at or past W1 are cleared: the scan leaves the groups
       // past the last window of the text unwritten
       const unsigned long long wl = w + static_cast<unsigned long long>(u * 32 + lane) * 32;
-      v[u] = 0u;
-      if (wl < W1) {
-        if (HC_IN_BOUNDS(wl / 32 < a.num_chunks * (a.C / 32))) v[u] = __ldcs(bits + wl / 32);
-        if (W1 - wl < 32) v[u] &= (1u << (W1 - wl)) - 1u;
-      }
+      if (wl < W1 && W1 - wl < 32) v[u] &= (1u << (W1 - wl)) - 1u;
     }
 #pragma unroll
     for (int u = 0; u < kBitmapWords; ++u) {
