@@ -473,7 +473,7 @@ KernelFn single_pass_init_kernel() { return hc_single_pass_init_kernel; }
 // measured slower on GB300 for the patterns this form serves: those with
 // many occurrences, where every round has bits.)
 namespace {
-constexpr int kBitmapWords = 8;
+constexpr int kBitmapWords = 4;
 constexpr int kBitmapRound = 1024;  // windows per round (32 lanes x 32 bits)
 }  // namespace
 
